@@ -1,0 +1,16 @@
+import os
+import sys
+
+# Small dense problems run fastest single-threaded; several BLAS pools
+# competing for the cores slow the oracle down by orders of magnitude.
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built library")
+    config.addinivalue_line("markers", "slow: takes more than a few seconds on the CPU")
