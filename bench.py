@@ -1,0 +1,415 @@
+#!/usr/bin/env python3
+"""Throughput of the superfast line-spectral-estimation hot path on GB300.
+
+One step = one complete fit (every step of Sec. III-D/III-E with the
+superfast evaluations of Sec. IV) of a batch of 64 synthetic instances with
+N = 4096 complex64 samples, K = 64 sinusoids (separation 2/N, alpha ~
+CN(0,1)), SNR uniform on [10, 30] dB per instance and an L = 4N = 16384
+point grid, in one launch of the persistent fit kernel.  The headline path
+is the mixed-precision one (FP64 Levinson recursion, generators, objective
+and updates; FP32 grid spectra and Newton sums); the plain FP64 path is
+timed on the same batch beside it.  Grid-point throughput (first column,
+Levinson recursion, Gohberg-Semencul apply and all six grid outputs, Sec.
+IV-D) is measured on the same batch at the fitted states.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank fits its own batch (weak scaling, no data-path
+collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "batch64_n4096_k64_l16384"
+METRIC = "grid-pt evals/s & fitted instances/s vs plain FP64 GPU path; serving p50/p99"
+B, N, K, L = 64, 4096, 64, 16384
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x DFMA/clk x 2 flop x max clock
+
+
+def levinson_flops(n: int) -> float:
+    """Algorithmic FP64 flops of one Levinson-Durbin factorisation of an n x n
+    Hermitian Toeplitz matrix as implemented: per order m, m complex
+    multiply-adds for the update and m for the next inner product (8 flops
+    each) -> sum_m 16 m = 8 n^2."""
+    return 8.0 * n * n
+
+
+def grid_bytes(n: int, l: int, f64: bool) -> float:
+    """Algorithmic bytes of one grid evaluation (Sec. IV-D): read rho and x
+    (n complex128 each) and write q, q', q'' (complex) and s, s', s'' (real)
+    at l points."""
+    es = 8 if f64 else 4
+    return 2 * 16.0 * n + l * (3 * 2 * es + 3 * es)
+
+
+# ----------------------------------------------------------------- clocks ---
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        import statistics
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------ CPU oracle ---
+ORACLE_SAMPLE = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from oracle import dense, fit as ofit
+from paper_1705_06073_gb300 import synth
+inst = synth.make_instance({N}, {K}, 20.0, 201)
+frac = {frac}
+t0 = time.perf_counter()
+ev = dense.DenseEval(inst.y, inst.theta, np.abs(inst.alpha) ** 2, inst.beta)
+ev.active_vectors()
+t_eval = time.perf_counter() - t0
+npts = int({L} * frac)
+t0 = time.perf_counter()
+ev.grid({L}, points=np.arange(npts) / {L})
+t_grid = (time.perf_counter() - t0) / frac
+# evaluations per fit of this instance family, counted by the oracle itself on
+# the same generator scaled down to N = {Np}, K = {Kp} (same K/N)
+t0 = time.perf_counter()
+counts = []
+for s in range(2):
+    small = synth.make_instance({Np}, {Kp}, 10.0 + 20.0 * s, 201 + s)
+    r = ofit.fit(small.y, 4 * {Np})
+    counts.append((r.n_evals, r.n_grid_evals))
+t_counts = time.perf_counter() - t0
+ne = float(np.mean([c[0] for c in counts])); ng = float(np.mean([c[1] for c in counts]))
+print(json.dumps(dict(t_eval=t_eval, t_grid=t_grid, n_evals=ne, n_grid=ng, t_counts=t_counts)))
+"""
+
+
+def oracle_sample(threads: int, frac: float = 1 / 16):
+    env = dict(os.environ, OPENBLAS_NUM_THREADS=str(threads), OMP_NUM_THREADS=str(threads),
+               CUDA_VISIBLE_DEVICES="")
+    code = ORACLE_SAMPLE.format(root=ROOT, N=N, K=K, L=L, frac=frac, Np=512, Kp=8)
+    t0 = time.perf_counter()
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1800)
+    wall = time.perf_counter() - t0
+    if out.returncode:
+        raise RuntimeError(out.stderr[-2000:])
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    per_fit = r["n_evals"] * r["t_eval"] + r["n_grid"] * r["t_grid"]
+    r["value"] = 1.0 / per_fit
+    r["wall"] = wall
+    return r
+
+
+def cpu_desc(r, threads):
+    return {"value": r["value"], "unit": "fitted instances/s", "cores": threads, "kind": "oracle",
+            "sample": (f"dense FP64 oracle on one instance of the workload (N={N}, K={K}): one full "
+                       f"evaluation (Cholesky, ln|C|, C^-1 y, eqs. q-x) took {r['t_eval']:.3f} s and one "
+                       f"{L}-point grid evaluation {r['t_grid']:.3f} s (timed on 1/16 of the points, "
+                       f"scaled); per-fit cost = {r['n_evals']:.1f} evaluations + {r['n_grid']:.1f} grid "
+                       f"evaluations, the counts of the oracle's own complete fits of the same generator "
+                       f"at N=512, K=8 (same K/N)")}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(threads, frac=1 / 64)
+        if i >= args.warmup:
+            vals.append(r)
+    import statistics
+    v = statistics.median([r["value"] for r in vals])
+    r = vals[-1]
+    desc = cpu_desc(dict(r, value=v), threads)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "fitted instances/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median([x["wall"] for x in vals]),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "B": B, "N": N, "K": K, "L": L, "l2": "n/a (CPU)"},
+            "cpu_baseline": desc,
+            "e2e": {"value": v, "unit": "fitted instances/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------- GPU arm ---
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1705_06073_gb300 import lse, synth
+
+    insts = synth.batch64_n4096(seed0=201 + 100000 * rank, B=B)
+    ys = [i.y for i, _ in insts]
+    offsets = np.concatenate([[0], np.cumsum([len(y) for y in ys])]).astype(np.int64)
+    y_host = np.ascontiguousarray(np.concatenate(ys))
+    y_d = torch.from_numpy(y_host).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+
+    def timed_fit(ctx, steps, warmup, out):
+        for _ in range(warmup):
+            lse.lse_fit_batch_d(ctx, y_d, offsets, out, stream)
+        stream.synchronize()
+        lse.lse_kernel_time(ctx, 0)
+        barrier()
+        ms = []
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                lse.lse_fit_batch_d(ctx, y_d, offsets, out, stream)
+                e1.record(stream)
+            stream.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        barrier()
+        kms, launches = lse.lse_kernel_time(ctx, 0)
+        return ms, kms, launches
+
+    def max_over_ranks(x: float) -> float:
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x: float) -> float:
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    res = {}
+    paths = [("mixed", lse.LSE_PREC_MIXED)] + ([] if args.no_fp64 else [("fp64", lse.LSE_PREC_FP64)])
+    ctxs = {}
+    for name, prec in paths:
+        ctx = lse.lse_create(lse.lse_config_default(device=local, precision=prec, grid_size=L))
+        ctxs[name] = ctx
+        out = lse.alloc_batch_out(offsets, device=dev)
+        if name == "mixed":
+            with ClockSampler(local) as clk:
+                ms, kms, launches = timed_fit(ctx, args.steps, args.warmup, out)
+            clocks = clk.summary()
+        else:
+            ms, kms, launches = timed_fit(ctx, args.steps, args.warmup, out)
+        n_ev = out["n_evals"].cpu().numpy()
+        n_gr = out["n_grid"].cpu().numpy()
+        st = out["status"].cpu().numpy()
+        Kf = out["K"].cpu().numpy()
+        total_ms = max_over_ranks(sum(ms))
+        res[name] = dict(ms=ms, total_ms=total_ms, kernel_ms=kms / max(launches, 1), launches=launches,
+                         n_evals=n_ev, n_grid=n_gr, status=st, K=Kf,
+                         value=sum_over_ranks(B * args.steps) / (total_ms / 1e3), out=out)
+
+    # ---- grid-point throughput at the fitted states (factor + grid kernels)
+    grid = {}
+    for name, prec in paths:
+        ctx = ctxs[name]
+        out = res[name]["out"]
+        f64 = name == "fp64"
+        Ks = out["K"].cpu().numpy().astype(np.int64)
+        ko = np.zeros(B + 1, np.int64)
+        th_l, ga_l = [], []
+        th_all = out["theta"].cpu().numpy()
+        ga_all = out["gamma"].cpu().numpy()
+        for b in range(B):
+            th_l.append(th_all[offsets[b]:offsets[b] + Ks[b]])
+            ga_l.append(ga_all[offsets[b]:offsets[b] + Ks[b]])
+            ko[b + 1] = ko[b] + Ks[b]
+        th_d = torch.from_numpy(np.concatenate(th_l + [np.zeros(1)])).to(dev)
+        ga_d = torch.from_numpy(np.concatenate(ga_l + [np.zeros(1)])).to(dev)
+        be_d = out["beta"].clone()
+        Ls = np.full(B, L, np.int32)
+        ct = torch.complex128 if f64 else torch.complex64
+        rt = torch.float64 if f64 else torch.float32
+        outs = {f: torch.empty(B * L, dtype=ct if f in ("q", "dq", "d2q") else rt, device=dev)
+                for f in ("q", "dq", "d2q", "s", "ds", "d2s")}
+        for _ in range(args.warmup):
+            lse.lse_eval_grid_batch_d(ctx, y_d, offsets, th_d, ga_d, ko, be_d, Ls, outs, f64, stream)
+        stream.synchronize()
+        lse.lse_kernel_time(ctx, 1)
+        lse.lse_kernel_time(ctx, 2)
+        barrier()
+        ms = []
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                lse.lse_eval_grid_batch_d(ctx, y_d, offsets, th_d, ga_d, ko, be_d, Ls, outs, f64, stream)
+                e1.record(stream)
+            stream.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        barrier()
+        fms, fl = lse.lse_kernel_time(ctx, 1)
+        gms, gl = lse.lse_kernel_time(ctx, 2)
+        tot = max_over_ranks(sum(ms))
+        grid[name] = dict(value=sum_over_ranks(B * L * args.steps) / (tot / 1e3), ms=tot / args.steps,
+                          factor_ms=fms / max(fl, 1), grid_ms=gms / max(gl, 1), launches=fl + gl)
+
+    # ---- end to end through the host API (pinned host inputs, results back)
+    ctx = ctxs["mixed"]
+    lse.lse_fit_batch(ctx, ys)  # warm the staging buffers
+    e2e_ms = []
+    for _ in range(max(1, min(args.steps, 3))):
+        barrier()
+        t0 = time.perf_counter()
+        lse.lse_fit_batch(ctx, ys)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_tot = max_over_ranks(sum(e2e_ms))
+    e2e_val = sum_over_ranks(B * len(e2e_ms)) / (e2e_tot / 1e3)
+    h2d = int(y_host.nbytes)  # y (complex64)
+    d2h = int(offsets[-1] * (8 + 8 + 16) + B * (8 + 8 + 4 * 5))  # theta, gamma, alpha slices + per-instance scalars
+
+    for c in ctxs.values():
+        lse.lse_destroy(c)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    m = res["mixed"]
+    # Levinson flops of one launch: every instance's evaluations in that fit
+    fit_flops = float(np.sum(m["n_evals"])) * levinson_flops(N)
+    achieved = fit_flops / (m["kernel_ms"] / 1e3) / 1e12
+    cpu = None
+    if not args.no_cpu:
+        threads = os.cpu_count() or 1
+        try:
+            cpu = cpu_desc(oracle_sample(threads), threads)
+        except Exception as e:  # the baseline is reported, never required
+            cpu = {"value": None, "error": str(e)[:300]}
+    gm = grid["mixed"]
+    line = {
+        "metric": METRIC,
+        "value": m["value"],
+        "unit": "fitted instances/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": m["total_ms"] / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64 recursion + f32 grid/sums (mixed)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "B": B, "N": N, "K": K, "L": L, "snr_db": "U[10,30]",
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"instances sharded x{world}"},
+        "clocks": clocks,
+        "gpu_launches": int(m["launches"]),
+        "e2e": {"value": e2e_val, "unit": "fitted instances/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "fit_kernel<mixed> (FP64 Levinson recursion dominates)",
+                     "peak_source": "nominal FP64 of the recipe: 152 SMs x 2 DFMA/clk x 2.07 GHz"},
+        "fit": {"iters_mean": None, "n_evals_mean": float(np.mean(m["n_evals"])),
+                "n_grid_mean": float(np.mean(m["n_grid"])), "K_mean": float(np.mean(m["K"])),
+                "status_nonzero": int(np.count_nonzero(m["status"])), "fit_kernel_ms": m["kernel_ms"]},
+        "grid_pt_evals": {"value": gm["value"], "unit": "grid-pt evals/s", "ms_per_batch": gm["ms"],
+                          "factor_kernel_ms": gm["factor_ms"], "grid_kernel_ms": gm["grid_ms"],
+                          "grid_kernel_hbm_gbs": B * grid_bytes(N, L, False) / (gm["grid_ms"] / 1e3) / 1e9},
+        "cpu_baseline": cpu,
+    }
+    if "fp64" in res:
+        f = res["fp64"]
+        gf = grid["fp64"]
+        line["fp64_path"] = {"value": f["value"], "unit": "fitted instances/s", "ms_per_step": f["total_ms"] / args.steps,
+                             "fit_kernel_ms": f["kernel_ms"], "n_evals_mean": float(np.mean(f["n_evals"])),
+                             "grid_pt_evals": gf["value"], "grid_kernel_ms": gf["grid_ms"],
+                             "factor_kernel_ms": gf["factor_ms"],
+                             "grid_kernel_hbm_gbs": B * grid_bytes(N, L, True) / (gf["grid_ms"] / 1e3) / 1e9}
+        line["mixed_over_fp64"] = {"fit": m["value"] / f["value"], "grid": gm["value"] / gf["value"]}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

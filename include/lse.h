@@ -1,0 +1,192 @@
+/*
+ * lse.h -- C ABI of the GB300 superfast line-spectral-estimation library.
+ *
+ * The method is the block-coordinate-descent estimator of Hansen, Fleury and
+ * Rao, "Superfast Line Spectral Estimation" (IEEE TSP 2018), complete-data
+ * case (Sec. IV, Phi = I, M = N): given y in C^N it estimates the model order
+ * K and, per component, the frequency theta_k in [0,1), the coefficient
+ * alpha_k and the variance gamma_k, plus the noise variance beta
+ * (Sec. III, eqs. model, estModel, obj).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * - Complex arrays are interleaved (re, im).  y is complex64; frequencies,
+ *   variances and coefficients are double.
+ * - Index n runs 0..N-1: [psi(theta)]_n = exp(j 2 pi n theta) (the paper's
+ *   n-1 for n = 1..N, eq. model).
+ * - The caller owns every buffer it passes.  Host-pointer entry points copy in
+ *   and out; the *_d entry points take device pointers and a cudaStream_t
+ *   (passed as void*), enqueue their work on that stream and return without
+ *   synchronising unless stated.
+ * - Errors are reported only through lse_status; nothing is thrown across
+ *   the ABI.  A context is not thread-safe: use one context per host thread.
+ */
+#ifndef LSE_H
+#define LSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LSE_API __attribute__((visibility("default")))
+#else
+#define LSE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lse_ctx lse_ctx;
+
+typedef enum lse_status {
+  LSE_OK = 0,
+  LSE_EINVAL = 1,    /* an argument is out of range (message via lse_last_error) */
+  LSE_ENOMEM = 2,    /* a device allocation failed */
+  LSE_EBUDGET = 3,   /* the request needs more device memory than hbm_budget_bytes */
+  LSE_ENUMERIC = 4,  /* the Levinson recursion met a pivot <= 0 or a non-finite value */
+  LSE_ENOTCONV = 5,  /* max_outer iterations reached; the current estimate is returned */
+  LSE_ETIMEOUT = 6,  /* a bounded device-side wait expired */
+  LSE_ECUDA = 7,     /* a CUDA runtime call failed */
+  LSE_ECAPACITY = 8  /* more components than the caller's capacity; K is set, arrays untouched */
+} lse_status;
+
+/* Arithmetic of the hot path.
+ * LSE_PREC_FP64: every step in FP64 (the plain path).
+ * LSE_PREC_MIXED: first column, Levinson recursion, Gohberg-Semencul apply,
+ *   objective, beta and gamma updates in FP64; grid FFTs, the grid
+ *   combine/search and the Newton sums in FP32 (complex64); grid decisions
+ *   are re-scored in FP64 before they are taken. */
+enum { LSE_PREC_FP64 = 0, LSE_PREC_MIXED = 1 };
+
+/* element type of grid outputs */
+enum { LSE_F32 = 0, LSE_F64 = 1 };
+
+typedef struct lse_config {
+  int32_t device;                  /* CUDA device ordinal */
+  int32_t precision;               /* LSE_PREC_FP64 or LSE_PREC_MIXED */
+  uint64_t hbm_budget_bytes;       /* cap on the context's device workspace; 0 = no cap */
+  int32_t grid_size;               /* L for lse_fit*: 0 = 8N rounded to the nearest power of two
+                                      (Sec. III-C5 footnote); > 0: that L (a power of two >= 2N) */
+  double tau;                      /* threshold adjustment of eq. (activate_criterion); paper: 5 */
+  int32_t max_outer;               /* outer-iteration cap (paper silent); default 200 */
+  int32_t max_inner;               /* (theta,gamma) updates per outer iteration (Sec. III-D): 5 */
+  int32_t approx_activation_iters; /* outer iterations that may use the approximate activation
+                                      of Sec. III-E; default 10; 0 disables it */
+  uint64_t flags;                  /* reserved, must be 0 */
+} lse_config;
+
+/* Fill cfg with the paper's defaults (device 0, FP64, tau = 5, ...). */
+LSE_API void lse_config_default(lse_config* cfg);
+
+/* Result of one fit.  K_cap, theta, alpha and gamma are set by the caller;
+ * everything else is written by the library.  Components are sorted by
+ * frequency.  alpha_k = gamma_k q_k is the posterior mean of eq. (bmu)
+ * (footnote to eq. bmu). */
+typedef struct lse_result {
+  int32_t K;          /* out: number of active components */
+  int32_t K_cap;      /* in: capacity of theta, gamma (K_cap) and alpha (2*K_cap) */
+  double* theta;      /* out [K_cap]: frequencies in [0,1), ascending */
+  double* alpha;      /* out [2*K_cap]: complex coefficients, interleaved */
+  double* gamma;      /* out [K_cap]: component variances > 0 */
+  double beta;        /* out: noise variance */
+  double objective;   /* out: eq. (obj) at the returned state, without the constant */
+  int32_t iters;      /* out: outer iterations run */
+  int32_t n_evals;    /* out: model evaluations (factorisations of C) */
+  int32_t n_grid;     /* out: grid evaluations (activation searches, Sec. III-C5) */
+} lse_result;
+
+/* Device-resident results of a batched fit.  Instance b owns the slice
+ * [off_b, off_b + N_b) of theta, gamma and alpha (complex, interleaved) where
+ * off_b is the instance's offset in the y batch: K <= N always (K_max = N,
+ * footnote in Sec. III-A), so the slice always fits.  All arrays are device
+ * memory owned by the caller. */
+typedef struct lse_batch_out {
+  double* theta;      /* [sum N_b] */
+  double* gamma;      /* [sum N_b] */
+  double* alpha;      /* [2 * sum N_b] */
+  int32_t* K;         /* [B] */
+  double* beta;       /* [B] */
+  double* objective;  /* [B] */
+  int32_t* iters;     /* [B] */
+  int32_t* n_evals;   /* [B] */
+  int32_t* n_grid;    /* [B] */
+  int32_t* status;    /* [B] lse_status per instance */
+} lse_batch_out;
+
+/* Create a context on cfg->device (cfg may be NULL for defaults).  The
+ * context owns its device workspace, twiddle tables and stream. */
+LSE_API lse_status lse_create(const lse_config* cfg, lse_ctx** out);
+
+/* Release everything the context owns.  NULL is accepted. */
+LSE_API void lse_destroy(lse_ctx* ctx);
+
+/* Static description of a status code. */
+LSE_API const char* lse_strerror(lse_status s);
+
+/* Detail of the last failing call on this context (empty if none). */
+LSE_API const char* lse_last_error(const lse_ctx* ctx);
+
+/* Fit one instance (Sec. III algorithm; superfast evaluations of Sec. IV).
+ * y: host, complex64 [2*N floats]; 2 <= N <= 131072.  On LSE_ECAPACITY out->K holds
+ * the number of components and the arrays are not written.  Blocks until the
+ * result is in out. */
+LSE_API lse_status lse_fit(lse_ctx* ctx, const float* y, int32_t N, lse_result* out);
+
+/* Fit B independent instances of possibly different N in one launch.
+ * y: host complex64, instance b = y[offsets[b] .. offsets[b+1]) (complex
+ * elements); offsets has B+1 entries, offsets[0] = 0.  outs[b] and
+ * per_instance[b] receive instance b's result and status; the return value
+ * is LSE_OK if the launch ran (instances fail independently) or the first
+ * launch-level error.  Blocks until done. */
+LSE_API lse_status lse_fit_batch(lse_ctx* ctx, const float* y, const int64_t* offsets, int32_t B,
+                         lse_result* outs, lse_status* per_instance);
+
+/* Device-pointer batched fit.  y_d: device complex64 batch; offsets: HOST
+ * array [B+1] as in lse_fit_batch; out: device arrays (lse_batch_out).
+ * stream: cudaStream_t (NULL = the context's stream).  Asynchronous: the
+ * results are valid once the stream has reached this point. */
+LSE_API lse_status lse_fit_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* offsets, int32_t B,
+                           const lse_batch_out* out, void* stream);
+
+/* Grid evaluation (Sec. IV-D): for C = beta I + sum_k gamma_k psi(theta_k)
+ * psi(theta_k)^H (eq. py), compute on theta_l = l/L, l = 0..L-1,
+ *   q(theta) = psi(theta)^H C^{-1} y,   s(theta) = psi(theta)^H C^{-1} psi(theta)
+ * and their first and second theta-derivatives.  All components given are
+ * active; the evaluation uses the full C (C_{~k} = C for a component that is
+ * not in the set, Sec. IV-D).  Host pointers; y complex64 [2N]; theta, gamma
+ * [K] (K >= 0); beta > 0; L a power of two with L >= 2N.  Outputs: q, dq, d2q
+ * complex [2L], s, ds, d2s real [L], element type dtype (LSE_F64 for an
+ * LSE_PREC_FP64 context, LSE_F32 for LSE_PREC_MIXED); any output may be NULL.
+ * Blocks until done. */
+LSE_API lse_status lse_eval_grid(lse_ctx* ctx, const float* y, int32_t N, const double* theta,
+                         const double* gamma, int32_t K, double beta, int32_t L, int32_t dtype,
+                         void* q, void* dq, void* d2q, void* s, void* ds, void* d2s);
+
+/* Batched device-pointer grid evaluation of B instances.
+ * y_d: device complex64, instance b at y_offsets[b] (HOST array [B+1]).
+ * theta_d, gamma_d: device double, instance b's components at
+ * k_offsets[b] .. k_offsets[b+1] (HOST array [B+1]).  beta_d: device double
+ * [B].  L: HOST int32 [B], each a power of two >= 2 N_b.  Outputs (device,
+ * any may be NULL): instance b's grid occupies [g_b, g_b + L_b) with g_b the
+ * prefix sum of L (complex outputs count complex elements).  dtype as for
+ * lse_eval_grid.  Asynchronous on stream (NULL = the context's stream). */
+LSE_API lse_status lse_eval_grid_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* y_offsets,
+                                 int32_t B, const double* theta_d, const double* gamma_d,
+                                 const int64_t* k_offsets, const double* beta_d,
+                                 const int32_t* L, int32_t dtype, void* q, void* dq, void* d2q,
+                                 void* s, void* ds, void* d2s, void* stream);
+
+/* Device time of this context's kernels, from CUDA events recorded on the
+ * launch stream around every launch since the previous call.  which: 0 = fit
+ * kernel, 1 = factorisation kernel (first column, Levinson recursion,
+ * Gohberg-Semencul apply), 2 = grid kernel.  Waits for the recorded events,
+ * writes the summed time in milliseconds and the number of launches, and
+ * clears the record. */
+LSE_API lse_status lse_kernel_time(lse_ctx* ctx, int32_t which, double* total_ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSE_H */

@@ -1,0 +1,501 @@
+// lse_api.cu -- the C ABI declared in include/lse.h: context, device memory,
+// argument checking, launches and host<->device staging.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lse.h"
+#include "lse_internal.h"
+
+using namespace lse;
+
+namespace {
+
+struct TimedLaunch {
+  cudaEvent_t a, b;
+};
+
+// Device buffer that only grows.
+struct DevBuf {
+  void* p = nullptr;
+  size_t n = 0;
+};
+
+}  // namespace
+
+struct lse_ctx {
+  lse_config cfg;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;
+  // twiddle tables exp(-j 2 pi k / 2^log2max)
+  c128* tw64 = nullptr;
+  c64* tw32 = nullptr;
+  int log2max = 0;
+  DevBuf ws, desc, counter, stage_in, stage_out, fac;
+  size_t allocated = 0;
+  InstDesc* h_desc = nullptr;  // pinned
+  size_t h_desc_cap = 0;
+  std::vector<TimedLaunch> timed[3];
+  std::string err;
+};
+
+namespace {
+
+lse_status fail(lse_ctx* c, lse_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+lse_status cuda_fail(lse_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, LSE_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define LSE_CUDA(ctx, call)                                  \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+lse_status ensure(lse_ctx* c, DevBuf& b, size_t bytes) {
+  if (b.n >= bytes) return LSE_OK;
+  const size_t grow = bytes - b.n;
+  if (c->cfg.hbm_budget_bytes && c->allocated + grow > c->cfg.hbm_budget_bytes)
+    return fail(c, LSE_EBUDGET, "request needs " + std::to_string(c->allocated + grow) +
+                                    " bytes of device memory, budget is " +
+                                    std::to_string((unsigned long long)c->cfg.hbm_budget_bytes));
+  if (b.p) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(b.p);
+    c->allocated -= b.n;
+    b.p = nullptr;
+    b.n = 0;
+  }
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    return fail(c, LSE_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  b.n = bytes;
+  c->allocated += bytes;
+  return LSE_OK;
+}
+
+__global__ void twiddle_kernel(c128* t64, c64* t32, int log2m) {
+  const int M = 1 << log2m;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi(2.0 * (double)k / (double)M, &s, &c);
+    t64[k] = mk(c, -s);
+    t32[k] = mk((float)c, (float)-s);
+  }
+}
+
+lse_status ensure_tables(lse_ctx* c, int log2m) {
+  if (log2m < 2) log2m = 2;
+  if (c->tw64 && c->log2max >= log2m) return LSE_OK;
+  if (c->tw64) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->tw64);
+    cudaFree(c->tw32);
+    c->tw64 = nullptr;
+    c->tw32 = nullptr;
+  }
+  const size_t M = size_t(1) << log2m;
+  LSE_CUDA(c, cudaMalloc(&c->tw64, M * sizeof(c128)));
+  LSE_CUDA(c, cudaMalloc(&c->tw32, M * sizeof(c64)));
+  twiddle_kernel<<<256, 256, 0, c->stream>>>(c->tw64, c->tw32, log2m);
+  LSE_CUDA(c, cudaGetLastError());
+  c->log2max = log2m;
+  return LSE_OK;
+}
+
+Tables tables(const lse_ctx* c) { return Tables{c->tw64, c->tw32, c->log2max}; }
+
+int default_L(int N) {
+  // 8N rounded to the nearest power of two (Sec. III-C5 footnote)
+  double l = std::log2(8.0 * N);
+  return 1 << (int)std::lround(l);
+}
+
+bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
+
+lse_status stage_desc(lse_ctx* c, const std::vector<InstDesc>& d) {
+  const size_t bytes = d.size() * sizeof(InstDesc);
+  if (c->h_desc_cap < d.size()) {
+    if (c->h_desc) cudaFreeHost(c->h_desc);
+    c->h_desc = nullptr;
+    LSE_CUDA(c, cudaMallocHost(&c->h_desc, bytes));
+    c->h_desc_cap = d.size();
+  }
+  lse_status s = ensure(c, c->desc, bytes);
+  if (s) return s;
+  // the previous launch may still read the pinned staging copy
+  LSE_CUDA(c, cudaStreamSynchronize(c->stream));
+  std::memcpy(c->h_desc, d.data(), bytes);
+  LSE_CUDA(c, cudaMemcpyAsync(c->desc.p, c->h_desc, bytes, cudaMemcpyHostToDevice, c->stream));
+  return LSE_OK;
+}
+
+void record(lse_ctx* c, int which, cudaStream_t st, bool start) {
+  if (start) {
+    TimedLaunch t;
+    cudaEventCreate(&t.a);
+    cudaEventCreate(&t.b);
+    cudaEventRecord(t.a, st);
+    c->timed[which].push_back(t);
+  } else {
+    cudaEventRecord(c->timed[which].back().b, st);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+void lse_config_default(lse_config* cfg) {
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->device = 0;
+  cfg->precision = LSE_PREC_FP64;
+  cfg->hbm_budget_bytes = 0;
+  cfg->grid_size = 0;
+  cfg->tau = 5.0;
+  cfg->max_outer = 200;
+  cfg->max_inner = 5;
+  cfg->approx_activation_iters = 10;
+  cfg->flags = 0;
+}
+
+const char* lse_strerror(lse_status s) {
+  switch (s) {
+    case LSE_OK: return "ok";
+    case LSE_EINVAL: return "invalid argument";
+    case LSE_ENOMEM: return "out of device memory";
+    case LSE_EBUDGET: return "request exceeds the device-memory budget";
+    case LSE_ENUMERIC: return "Levinson recursion broke down (covariance not numerically positive definite)";
+    case LSE_ENOTCONV: return "iteration limit reached before convergence";
+    case LSE_ETIMEOUT: return "device-side wait timed out";
+    case LSE_ECUDA: return "CUDA runtime error";
+    case LSE_ECAPACITY: return "result capacity too small";
+  }
+  return "unknown status";
+}
+
+const char* lse_last_error(const lse_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+lse_status lse_create(const lse_config* cfg, lse_ctx** out) {
+  if (!out) return LSE_EINVAL;
+  *out = nullptr;
+  lse_config c;
+  if (cfg) c = *cfg; else lse_config_default(&c);
+  if (c.precision != LSE_PREC_FP64 && c.precision != LSE_PREC_MIXED) return LSE_EINVAL;
+  if (c.max_outer < 1 || c.max_inner < 0 || c.approx_activation_iters < 0 || !(c.tau >= 0.0) || c.flags)
+    return LSE_EINVAL;
+  if (c.grid_size < 0 || (c.grid_size > 0 && !is_pow2(c.grid_size))) return LSE_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev) return LSE_ECUDA;
+  if (cudaSetDevice(c.device) != cudaSuccess) return LSE_ECUDA;
+  lse_ctx* ctx = new lse_ctx();
+  ctx->cfg = c;
+  cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, c.device);
+  if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete ctx;
+    return LSE_ECUDA;
+  }
+  lse_status s = ensure_tables(ctx, 17);
+  if (s == LSE_OK) s = ensure(ctx, ctx->counter, 256);
+  if (s != LSE_OK) {
+    lse_destroy(ctx);
+    return s;
+  }
+  *out = ctx;
+  return LSE_OK;
+}
+
+void lse_destroy(lse_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->cfg.device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (DevBuf* b : {&ctx->ws, &ctx->desc, &ctx->counter, &ctx->stage_in, &ctx->stage_out, &ctx->fac})
+    if (b->p) cudaFree(b->p);
+  if (ctx->tw64) cudaFree(ctx->tw64);
+  if (ctx->tw32) cudaFree(ctx->tw32);
+  if (ctx->h_desc) cudaFreeHost(ctx->h_desc);
+  for (auto& v : ctx->timed)
+    for (auto& t : v) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+lse_status lse_kernel_time(lse_ctx* ctx, int32_t which, double* total_ms, int64_t* launches) {
+  if (!ctx || which < 0 || which > 2) return LSE_EINVAL;
+  double tot = 0.0;
+  int64_t n = 0;
+  for (auto& t : ctx->timed[which]) {
+    LSE_CUDA(ctx, cudaEventSynchronize(t.b));
+    float ms = 0.f;
+    LSE_CUDA(ctx, cudaEventElapsedTime(&ms, t.a, t.b));
+    tot += ms;
+    ++n;
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  ctx->timed[which].clear();
+  if (total_ms) *total_ms = tot;
+  if (launches) *launches = n;
+  return LSE_OK;
+}
+
+lse_status lse_fit_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* offsets, int32_t B,
+                           const lse_batch_out* out, void* stream) {
+  if (!ctx || !y_d || !offsets || B < 1 || !out) return fail(ctx, LSE_EINVAL, "null argument or B < 1");
+  if (offsets[0] != 0) return fail(ctx, LSE_EINVAL, "offsets[0] must be 0");
+  cudaSetDevice(ctx->cfg.device);
+  cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+  std::vector<InstDesc> d(B);
+  int Nmax = 0, Lmax = 0;
+  for (int b = 0; b < B; ++b) {
+    const int64_t n = offsets[b + 1] - offsets[b];
+    if (n < 2 || n > (1 << 17)) return fail(ctx, LSE_EINVAL, "instance " + std::to_string(b) + ": N out of range");
+    const int N = (int)n;
+    const int L = ctx->cfg.grid_size ? ctx->cfg.grid_size : default_L(N);
+    if (L < 2 * N) return fail(ctx, LSE_EINVAL, "grid size L must be >= 2N");
+    d[b] = InstDesc{offsets[b], N, L, 0, 0, 0, 0};
+    Nmax = std::max(Nmax, N);
+    Lmax = std::max(Lmax, L);
+  }
+  const bool mixed = ctx->cfg.precision == LSE_PREC_MIXED;
+  lse_status s = ensure_tables(ctx, std::max(ilog2((uint32_t)Lmax), ilog2(2u * (uint32_t)Nmax)));
+  if (s) return s;
+  const int grid = std::min(B, ctx->sm_count);
+  const size_t per = fit_workspace_bytes(Nmax, Lmax, mixed);
+  if ((s = ensure(ctx, ctx->ws, per * grid))) return s;
+  if ((s = stage_desc(ctx, d))) return s;
+  if (st != ctx->stream) {
+    cudaEvent_t e;
+    LSE_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaEventRecord(e, ctx->stream);
+    cudaStreamWaitEvent(st, e, 0);
+    cudaEventDestroy(e);
+  }
+  LSE_CUDA(ctx, cudaMemsetAsync(ctx->counter.p, 0, sizeof(int), st));
+  FitConfig fc{ctx->cfg.tau, ctx->cfg.max_outer, ctx->cfg.max_inner, ctx->cfg.approx_activation_iters};
+  FitOut fo{out->theta, out->gamma, (c128*)out->alpha, out->K, out->beta, out->objective, out->iters,
+            out->n_evals, out->n_grid, out->status};
+  record(ctx, 0, st, true);
+  cudaError_t e = launch_fit(mixed, y_d, (const InstDesc*)ctx->desc.p, B, Nmax, Lmax, fc, tables(ctx), fo, ctx->ws.p,
+                             (int*)ctx->counter.p, grid, st);
+  record(ctx, 0, st, false);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "fit kernel launch");
+  if (st != ctx->stream) {
+    // later host-side staging on the context stream must follow this launch
+    cudaEvent_t ev;
+    LSE_CUDA(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaEventRecord(ev, st);
+    cudaStreamWaitEvent(ctx->stream, ev, 0);
+    cudaEventDestroy(ev);
+  }
+  return LSE_OK;
+}
+
+lse_status lse_fit_batch(lse_ctx* ctx, const float* y, const int64_t* offsets, int32_t B, lse_result* outs,
+                         lse_status* per_instance) {
+  if (!ctx || !y || !offsets || B < 1 || !outs) return fail(ctx, LSE_EINVAL, "null argument or B < 1");
+  cudaSetDevice(ctx->cfg.device);
+  const int64_t tot = offsets[B];
+  if (tot <= 0) return fail(ctx, LSE_EINVAL, "empty batch");
+  // device staging: y | theta | gamma | alpha | K | beta | obj | iters | nevals | status
+  const size_t yb = (size_t)tot * 2 * sizeof(float);
+  const size_t ob = (size_t)tot * (2 + 2) * sizeof(double) + (size_t)B * (5 * sizeof(int) + 2 * sizeof(double)) + 1024;
+  lse_status s;
+  if ((s = ensure(ctx, ctx->stage_in, yb))) return s;
+  if ((s = ensure(ctx, ctx->stage_out, ob))) return s;
+  char* o = (char*)ctx->stage_out.p;
+  lse_batch_out bo;
+  bo.theta = (double*)o; o += tot * sizeof(double);
+  bo.gamma = (double*)o; o += tot * sizeof(double);
+  bo.alpha = (double*)o; o += tot * 2 * sizeof(double);
+  bo.beta = (double*)o; o += B * sizeof(double);
+  bo.objective = (double*)o; o += B * sizeof(double);
+  bo.K = (int32_t*)o; o += B * sizeof(int);
+  bo.iters = (int32_t*)o; o += B * sizeof(int);
+  bo.n_evals = (int32_t*)o; o += B * sizeof(int);
+  bo.n_grid = (int32_t*)o; o += B * sizeof(int);
+  bo.status = (int32_t*)o; o += B * sizeof(int);
+  LSE_CUDA(ctx, cudaMemcpyAsync(ctx->stage_in.p, y, yb, cudaMemcpyHostToDevice, ctx->stream));
+  if ((s = lse_fit_batch_d(ctx, (const float*)ctx->stage_in.p, offsets, B, &bo, ctx->stream))) return s;
+  std::vector<char> host(ob);
+  LSE_CUDA(ctx, cudaMemcpyAsync(host.data(), ctx->stage_out.p, ob, cudaMemcpyDeviceToHost, ctx->stream));
+  LSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const char* h = host.data();
+  const double* th = (const double*)h;
+  const double* ga = th + tot;
+  const double* al = ga + tot;
+  const double* be = al + 2 * tot;
+  const double* ob_ = be + B;
+  const int32_t* K = (const int32_t*)(ob_ + B);
+  const int32_t* it = K + B;
+  const int32_t* ne = it + B;
+  const int32_t* ng = ne + B;
+  const int32_t* stt = ng + B;
+  for (int b = 0; b < B; ++b) {
+    lse_result& r = outs[b];
+    lse_status sb = (lse_status)stt[b];
+    r.K = K[b];
+    r.beta = be[b];
+    r.objective = ob_[b];
+    r.iters = it[b];
+    r.n_evals = ne[b];
+    r.n_grid = ng[b];
+    if (K[b] > r.K_cap) {
+      sb = LSE_ECAPACITY;
+    } else {
+      const int64_t off = offsets[b];
+      for (int k = 0; k < K[b]; ++k) {
+        if (r.theta) r.theta[k] = th[off + k];
+        if (r.gamma) r.gamma[k] = ga[off + k];
+        if (r.alpha) { r.alpha[2 * k] = al[2 * (off + k)]; r.alpha[2 * k + 1] = al[2 * (off + k) + 1]; }
+      }
+    }
+    if (per_instance) per_instance[b] = sb;
+  }
+  return LSE_OK;
+}
+
+lse_status lse_fit(lse_ctx* ctx, const float* y, int32_t N, lse_result* out) {
+  if (!ctx || !y || !out || N < 2) return fail(ctx, LSE_EINVAL, "null argument or N < 2");
+  const int64_t off[2] = {0, N};
+  lse_status per = LSE_OK;
+  lse_status s = lse_fit_batch(ctx, y, off, 1, out, &per);
+  return s ? s : per;
+}
+
+lse_status lse_eval_grid_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* y_offsets, int32_t B,
+                                 const double* theta_d, const double* gamma_d, const int64_t* k_offsets,
+                                 const double* beta_d, const int32_t* L, int32_t dtype, void* q, void* dq, void* d2q,
+                                 void* s, void* ds, void* d2s, void* stream) {
+  if (!ctx || !y_d || !y_offsets || !k_offsets || !beta_d || !L || B < 1)
+    return fail(ctx, LSE_EINVAL, "null argument or B < 1");
+  const bool f32 = ctx->cfg.precision == LSE_PREC_MIXED;
+  if (dtype != (f32 ? LSE_F32 : LSE_F64))
+    return fail(ctx, LSE_EINVAL, "dtype must be LSE_F64 for an FP64 context and LSE_F32 for a mixed one");
+  cudaSetDevice(ctx->cfg.device);
+  cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+  std::vector<InstDesc> d(B);
+  int Nmax = 0, Lmax = 0;
+  int64_t g = 0;
+  for (int b = 0; b < B; ++b) {
+    const int64_t n = y_offsets[b + 1] - y_offsets[b];
+    const int64_t k = k_offsets[b + 1] - k_offsets[b];
+    if (n < 2 || n > (1 << 17) || k < 0 || k > n)
+      return fail(ctx, LSE_EINVAL, "instance " + std::to_string(b) + ": N or K out of range");
+    if (!is_pow2(L[b]) || L[b] < 2 * n) return fail(ctx, LSE_EINVAL, "L must be a power of two >= 2N");
+    d[b] = InstDesc{y_offsets[b], (int)n, L[b], k_offsets[b], (int)k, 0, g};
+    g += L[b];
+    Nmax = std::max(Nmax, (int)n);
+    Lmax = std::max(Lmax, (int)L[b]);
+  }
+  lse_status sst = ensure_tables(ctx, std::max(ilog2((uint32_t)Lmax), ilog2(2u * (uint32_t)Nmax)));
+  if (sst) return sst;
+  const int64_t totN = y_offsets[B];
+  const size_t fws = factor_workspace_bytes(Nmax) * B;
+  const size_t gws_hdr = ((size_t)B * sizeof(int64_t) + 255) & ~size_t(255);
+  const size_t gws = grid_workspace_bytes(B, g, f32);
+  const size_t fac_bytes = (size_t)totN * 2 * sizeof(c128) + (size_t)B * (sizeof(double) + sizeof(int)) + 512;
+  if ((sst = ensure(ctx, ctx->ws, std::max(fws, gws_hdr + gws)))) return sst;
+  if ((sst = ensure(ctx, ctx->fac, fac_bytes))) return sst;
+  if ((sst = stage_desc(ctx, d))) return sst;
+  // grid workspace offsets (bytes from the workspace base)
+  std::vector<int64_t> woff(B);
+  {
+    size_t o = gws_hdr;
+    const size_t es = f32 ? sizeof(c64) : sizeof(c128);
+    for (int b = 0; b < B; ++b) { woff[b] = (int64_t)o; o += (size_t)L[b] * 2 * 5 * es; }
+  }
+  if (st != ctx->stream) {
+    cudaEvent_t e;
+    LSE_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaEventRecord(e, ctx->stream);
+    cudaStreamWaitEvent(st, e, 0);
+    cudaEventDestroy(e);
+  }
+  c128* rho = (c128*)ctx->fac.p;
+  c128* x = rho + totN;
+  double* delta = (double*)(x + totN);
+  int* status = (int*)(delta + B);
+  record(ctx, 1, st, true);
+  cudaError_t e = launch_factor(y_d, (const InstDesc*)ctx->desc.p, B, Nmax, theta_d, gamma_d, beta_d, tables(ctx),
+                                ctx->ws.p, rho, x, delta, status, st);
+  record(ctx, 1, st, false);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "factor kernel launch");
+  // the grid kernel reuses the workspace; its offset table goes first
+  LSE_CUDA(ctx, cudaMemcpyAsync(ctx->ws.p, woff.data(), B * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  record(ctx, 2, st, true);
+  e = launch_grid(f32, (const InstDesc*)ctx->desc.p, B, Lmax, rho, x, delta, tables(ctx), ctx->ws.p, q, dq, d2q, s,
+                  ds, d2s, st);
+  record(ctx, 2, st, false);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "grid kernel launch");
+  if (st != ctx->stream) {
+    cudaEvent_t ev;
+    LSE_CUDA(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaEventRecord(ev, st);
+    cudaStreamWaitEvent(ctx->stream, ev, 0);
+    cudaEventDestroy(ev);
+  }
+  return LSE_OK;
+}
+
+lse_status lse_eval_grid(lse_ctx* ctx, const float* y, int32_t N, const double* theta, const double* gamma,
+                         int32_t K, double beta, int32_t L, int32_t dtype, void* q, void* dq, void* d2q, void* s,
+                         void* ds, void* d2s) {
+  if (!ctx || !y || N < 2 || K < 0 || K > N || (K > 0 && (!theta || !gamma)) || !(beta > 0.0))
+    return fail(ctx, LSE_EINVAL, "bad argument");
+  const bool f32 = ctx->cfg.precision == LSE_PREC_MIXED;
+  if (dtype != (f32 ? LSE_F32 : LSE_F64))
+    return fail(ctx, LSE_EINVAL, "dtype must be LSE_F64 for an FP64 context and LSE_F32 for a mixed one");
+  if (!is_pow2(L) || L < 2 * N) return fail(ctx, LSE_EINVAL, "L must be a power of two >= 2N");
+  cudaSetDevice(ctx->cfg.device);
+  const size_t es = f32 ? sizeof(float) : sizeof(double);
+  const size_t yb = (size_t)N * 2 * sizeof(float);
+  const size_t pb = ((size_t)2 * K + 1) * sizeof(double);
+  const size_t outb = (size_t)L * 9 * es;
+  lse_status st;
+  if ((st = ensure(ctx, ctx->stage_in, yb + pb + 512))) return st;
+  if ((st = ensure(ctx, ctx->stage_out, outb + 512))) return st;
+  char* in = (char*)ctx->stage_in.p;
+  float* yd = (float*)in;
+  double* thd = (double*)(in + ((yb + 255) & ~size_t(255)));
+  double* gad = thd + K;
+  double* bed = gad + K;
+  LSE_CUDA(ctx, cudaMemcpyAsync(yd, y, yb, cudaMemcpyHostToDevice, ctx->stream));
+  if (K) {
+    LSE_CUDA(ctx, cudaMemcpyAsync(thd, theta, K * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    LSE_CUDA(ctx, cudaMemcpyAsync(gad, gamma, K * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  }
+  LSE_CUDA(ctx, cudaMemcpyAsync(bed, &beta, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  char* o = (char*)ctx->stage_out.p;
+  void* dev[6];
+  void* host[6] = {q, dq, d2q, s, ds, d2s};
+  const size_t sz[6] = {2 * L * es, 2 * L * es, 2 * L * es, L * es, L * es, L * es};
+  for (int i = 0; i < 6; ++i) {
+    dev[i] = host[i] ? (void*)o : nullptr;
+    o += sz[i];
+  }
+  const int64_t yo[2] = {0, N}, ko[2] = {0, K};
+  const int32_t Ls[1] = {L};
+  if ((st = lse_eval_grid_batch_d(ctx, yd, yo, 1, thd, gad, ko, bed, Ls, dtype, dev[0], dev[1], dev[2], dev[3],
+                                  dev[4], dev[5], ctx->stream)))
+    return st;
+  for (int i = 0; i < 6; ++i)
+    if (host[i]) LSE_CUDA(ctx, cudaMemcpyAsync(host[i], dev[i], sz[i], cudaMemcpyDeviceToHost, ctx->stream));
+  int fst = 0;
+  const int* status = (const int*)((double*)((c128*)ctx->fac.p + 2 * (size_t)N) + 1);
+  LSE_CUDA(ctx, cudaMemcpyAsync(&fst, status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  LSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (fst) return fail(ctx, LSE_ENUMERIC, "Levinson recursion broke down");
+  return LSE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,654 @@
+// lse_fit.cu -- persistent fit kernel: one thread block runs the whole
+// block-coordinate-descent estimator (Sec. III-D, III-E of Hansen, Fleury,
+// Rao, "Superfast Line Spectral Estimation") for one instance at a time,
+// pulling instances from a device work counter, with every model evaluation
+// done by the superfast route of Sec. IV (Levinson recursion for the
+// Gohberg-Semencul generators, FFT convolutions, FFT grid, direct off-grid
+// sums).
+//
+// Readings of the paper (the same ones the CPU oracle follows):
+//  - (theta, gamma) update: one per-component diagonal Newton step with the
+//    diagonal Hessian of eqs. (derivative2) (non-positive entries replaced by
+//    (50N)^2 and gamma^-2, Sec. III-C1), step cut to 0.99 of the distance at
+//    which a gamma would reach 0, Armijo backtracking (c = 1e-4, <= 30
+//    halvings) on ln|C| + y^H C^{-1} y; theta modulo 1.
+//  - step 4 runs <= max_inner iterations and stops after the iteration whose
+//    squared Newton decrement is below N 1e-8 (that iteration takes no step
+//    but still checks deactivation).
+//  - deactivation removes, one at a time, the qualifying component whose
+//    removal lowers eq. (obj) most (ties: earliest activated).
+//  - gamma-bar is the mean active gamma, or the candidate's own
+//    eq. (activate_gamma) value when no component is active.
+//  - approximate activation runs in outer iterations 1..approx_iters while it
+//    activates something; candidates are cyclic local minima
+//    (strict on the left) with Delta L <= Delta L_min / 5 < 0, visited in
+//    ascending Delta L; a pass that activates nothing falls through to exact
+//    activation, which the later iterations use.
+//  - eps_beta = 1e-12 ||y||^2/N, eps_L = 2^-52, K_max = N, termination when
+//    the objective changes by less than N 1e-7 over an outer iteration.
+#include <cfloat>
+
+#include "lse_device.cuh"
+#include "lse_internal.h"
+
+namespace lse {
+
+namespace {
+
+constexpr int kNT = 256;         // threads per block
+constexpr int kSmemBytes = 200 * 1024;
+constexpr double kEpsL = 2.220446049250313e-16;
+constexpr int kST_OK = 0, kST_NUMERIC = 4, kST_NOTCONV = 5;
+
+struct FitShared {
+  c128 red[kNT];
+  MinLoc ml[kNT / 32];
+  double dred[kNT / 32];
+  LevShared lev;
+  // instance state (written by thread 0, read by all after a barrier)
+  int inst, K, status, n_evals, n_grid, cand_count, flag;
+  double beta, zeta, eps_beta, tau;
+  double logdet, yCy, delta_last, f_cur, yy;
+  double lpo, gbar;
+};
+
+// Per-block global workspace for an instance of size up to (Nmax, Lmax).
+template <class TG>
+struct Work {
+  c128 *y, *c, *a, *rho, *x, *Yf;
+  c128* buf[5];   // FFT buffers, M2max each (GS apply)
+  cx<TG>* gbuf[4];  // grid FFT buffers, Lmax each
+  double *theta, *gamma, *th_t, *ga_t, *dth, *dga;
+  c128* sums;     // 7 * Nmax
+  double* dl;     // Lmax
+  int* cand;      // Lmax
+};
+
+struct Layout {
+  size_t off[32];
+  size_t total;
+};
+
+template <class TG>
+__host__ __device__ inline Layout make_layout(int Nmax, int Lmax) {
+  Layout L;
+  const int M2 = 1 << ilog2(2u * (uint32_t)Nmax);
+  size_t o = 0;
+  int i = 0;
+  auto put = [&](size_t bytes) { L.off[i++] = o; o += (bytes + 255) & ~size_t(255); };
+  for (int j = 0; j < 6; ++j) put(sizeof(c128) * (size_t)Nmax);       // y c a rho x (+1 spare)
+  put(sizeof(c128) * (size_t)M2);                                       // Yf
+  for (int j = 0; j < 5; ++j) put(sizeof(c128) * (size_t)M2);          // buf
+  for (int j = 0; j < 4; ++j) put(sizeof(cx<TG>) * (size_t)Lmax);      // gbuf
+  for (int j = 0; j < 6; ++j) put(sizeof(double) * (size_t)Nmax);      // theta..dga
+  put(sizeof(c128) * 7 * (size_t)Nmax);                                 // sums
+  put(sizeof(double) * (size_t)Lmax);                                   // dl
+  put(sizeof(int) * (size_t)Lmax);                                      // cand
+  L.total = o;
+  return L;
+}
+
+template <class TG>
+__device__ Work<TG> carve(char* base, int Nmax, int Lmax) {
+  Layout L = make_layout<TG>(Nmax, Lmax);
+  Work<TG> w;
+  int i = 0;
+  w.y = (c128*)(base + L.off[i++]);
+  w.c = (c128*)(base + L.off[i++]);
+  w.a = (c128*)(base + L.off[i++]);
+  w.rho = (c128*)(base + L.off[i++]);
+  w.x = (c128*)(base + L.off[i++]);
+  i++;
+  w.Yf = (c128*)(base + L.off[i++]);
+  for (int j = 0; j < 5; ++j) w.buf[j] = (c128*)(base + L.off[i++]);
+  for (int j = 0; j < 4; ++j) w.gbuf[j] = (cx<TG>*)(base + L.off[i++]);
+  w.theta = (double*)(base + L.off[i++]);
+  w.gamma = (double*)(base + L.off[i++]);
+  w.th_t = (double*)(base + L.off[i++]);
+  w.ga_t = (double*)(base + L.off[i++]);
+  w.dth = (double*)(base + L.off[i++]);
+  w.dga = (double*)(base + L.off[i++]);
+  w.sums = (c128*)(base + L.off[i++]);
+  w.dl = (double*)(base + L.off[i++]);
+  w.cand = (int*)(base + L.off[i++]);
+  return w;
+}
+
+struct FitArgs {
+  const float* y;
+  const InstDesc* inst;
+  int B, Nmax, Lmax;
+  FitConfig cfg;
+  Tables tab;
+  FitOut out;
+  char* ws;
+  size_t ws_bytes;
+  int* counter;
+};
+
+__device__ __forceinline__ double prior_term(int K, int N, double zeta) {
+  const double a = K ? K * log(zeta) : 0.0;
+  const double b = (N - K) ? (N - K) * log1p(-zeta) : 0.0;
+  return a + b;
+}
+
+__device__ __forceinline__ double log_prior_odds(double zeta) {
+  return zeta <= 0.0 ? HUGE_VAL : log1p(-zeta) - log(zeta);
+}
+
+__device__ __forceinline__ double mod1(double t) {
+  double r = t - floor(t);
+  if (r >= 1.0) r -= 1.0;
+  return r;
+}
+
+template <bool MIXED>
+struct Fitter {
+  using TG = typename std::conditional<MIXED, float, double>::type;
+  FitShared* sh;
+  char* dsm;  // dynamic shared memory
+  Work<TG> w;
+  const FitArgs* A;
+  int N, L, log2L, log2M2;
+  bool lev_smem;
+  c128 *lev_c, *lev_a, *tables;
+  Twiddles<double> tw64;
+  Twiddles<TG> twg;
+
+  // ---------------------------------------------------------------- eval ---
+  // One evaluation of the model at (theta, gamma, beta): ln|C|, y^H C^{-1} y,
+  // rho, x = C^{-1} y and (optionally) the off-grid sums.  Returns 0 or 1
+  // (Levinson breakdown).
+  __device__ int evaluate(const double* th, const double* ga, int K, bool want_sums) {
+    const double beta = sh->beta;
+    block_first_column<kNT>(lev_c, th, ga, K, beta, N, tables);
+    LevResult lr = block_levinson<kNT>(lev_c, lev_a, N, sh->red, &sh->lev);
+    if (threadIdx.x == 0) sh->n_evals++;
+    if (lr.status) {
+      __syncthreads();
+      return 1;
+    }
+    for (int n = threadIdx.x; n < N; n += kNT) w.rho[n] = conj(lev_a[N - 1 - n]);
+    __syncthreads();
+    c128* bufs[5] = {w.buf[0], w.buf[1], w.buf[2], w.buf[3], w.buf[4]};
+    block_gs_apply<kNT>(w.rho, w.Yf, w.x, N, log2M2, lr.delta_last, bufs, tw64);
+    double part = 0.0;
+    for (int n = threadIdx.x; n < N; n += kNT) part += (conj(w.y[n]) * w.x[n]).re;
+    const double yCy = block_sum<kNT>(part, sh->dred);
+    if (threadIdx.x == 0) {
+      sh->logdet = lr.logdet;
+      sh->yCy = yCy;
+      sh->delta_last = lr.delta_last;
+      sh->f_cur = lr.logdet + yCy;
+    }
+    __syncthreads();
+    if (want_sums && K > 0) block_active_sums<kNT, double>(w.rho, w.x, th, K, N, w.sums);
+    return 0;
+  }
+
+  __device__ void compute_sums(int K) {
+    if (K > 0) block_active_sums<kNT, double>(w.rho, w.x, w.theta, K, N, w.sums);
+  }
+
+  // ---------------------------------------------------------------- grid ---
+  // q(theta_l), s(theta_l) on the L-point grid (Sec. IV-D) from length-L FFTs:
+  //   Q0 = FFT(rho), Q1 = FFT((n-c) rho_n), q = FFT(x), s = 2 Re(Q1 conj Q0)/delta
+  // and Delta L(theta_l) of eq. (delta_L) with gamma-bar = gbar (K > 0) or the
+  // point's own eq. (activate_gamma) value (K = 0).  Fills w.dl.
+  __device__ void grid_delta(int K) {
+    if (threadIdx.x == 0) sh->n_grid++;
+    const double cen = 0.5 * (double)(N - 2);
+    const c128* rho = w.rho;
+    const c128* x = w.x;
+    const int n_ = N;
+    block_fft<kNT, TG>([=] __device__(int i) { return i < n_ ? cvt<TG>(rho[i]) : zero<TG>(); }, w.gbuf[0], w.gbuf[3],
+                       log2L, false, twg);
+    block_fft<kNT, TG>([=] __device__(int i) { return i < n_ ? cvt<TG>(((double)i - cen) * rho[i]) : zero<TG>(); },
+                       w.gbuf[1], w.gbuf[3], log2L, false, twg);
+    block_fft<kNT, TG>([=] __device__(int i) { return i < n_ ? cvt<TG>(x[i]) : zero<TG>(); }, w.gbuf[2], w.gbuf[3],
+                       log2L, false, twg);
+    double gsum = 0.0;
+    for (int k = threadIdx.x; k < K; k += kNT) gsum += w.gamma[k];
+    gsum = block_sum<kNT>(gsum, sh->dred);
+    const double gbar = K ? gsum / K : 0.0;
+    const double lpo = log_prior_odds(sh->zeta);
+    const double inv_delta = 1.0 / sh->delta_last;
+    for (int l = threadIdx.x; l < L; l += kNT) {
+      const c128 Q0 = cvt<double>(w.gbuf[0][l]), Q1 = cvt<double>(w.gbuf[1][l]), q = cvt<double>(w.gbuf[2][l]);
+      const double s = 2.0 * inv_delta * (Q1 * conj(Q0)).re;
+      const double aq2 = norm2(q);
+      double gb = gbar;
+      if (K == 0) gb = aq2 > s ? (aq2 - s) / (s * s) : 0.0;
+      w.dl[l] = log1p(gb * s) + lpo - gb * aq2 / (1.0 + gb * s);
+    }
+    if (threadIdx.x == 0) {
+      sh->gbar = gbar;
+      sh->lpo = lpo;
+    }
+    __syncthreads();
+  }
+
+  __device__ void grid_point(int l, double& s, c128& q) const {
+    const c128 Q0 = cvt<double>(w.gbuf[0][l]), Q1 = cvt<double>(w.gbuf[1][l]);
+    q = cvt<double>(w.gbuf[2][l]);
+    s = 2.0 / sh->delta_last * (Q1 * conj(Q0)).re;
+  }
+
+  // ---------------------------------------------------- exact activation ---
+  __device__ int exact_activation(bool have_grid) {
+    int n_act = 0;
+    while (sh->K < N && sh->zeta > 0.0 && sh->status == kST_OK) {
+      const int K = sh->K;
+      if (!have_grid) grid_delta(K);
+      have_grid = false;
+      MinLoc m{HUGE_VAL, 0x7fffffff};
+      for (int l = threadIdx.x; l < L; l += kNT) m = minloc(m, MinLoc{w.dl[l], l});
+      m = block_minloc<kNT>(m, sh->ml);
+      if (threadIdx.x == 0) {
+        double s;
+        c128 q;
+        grid_point(m.i, s, q);
+        const double aq2 = norm2(q);
+        const double ghat = aq2 > s ? (aq2 - s) / (s * s) : 0.0;
+        const double gb = K ? sh->gbar : ghat;
+        const double gs = gb * s;
+        const double rhs = (1.0 + 1.0 / gs) * (log1p(gs) + sh->lpo) + sh->tau;
+        const bool ok = ghat > 0.0 && m.v < -kEpsL && aq2 / s > rhs;
+        sh->flag = ok;
+        if (ok) {
+          w.theta[K] = (double)m.i / (double)L;
+          w.gamma[K] = ghat;
+          sh->K = K + 1;
+        }
+      }
+      __syncthreads();
+      if (!sh->flag) break;
+      ++n_act;
+      if (evaluate(w.theta, w.gamma, sh->K, true)) {
+        if (threadIdx.x == 0) sh->status = kST_NUMERIC;
+        __syncthreads();
+      }
+    }
+    return n_act;
+  }
+
+  // ---------------------------------------------- approximate activation ---
+  // One pass of the scheme of Sec. III-E.  Returns the number activated.
+  __device__ int approximate_activation(bool& grid_valid) {
+    grid_valid = false;
+    if (sh->zeta <= 0.0 || sh->K >= N) return 0;
+    const int K0 = sh->K;
+    grid_delta(K0);
+    grid_valid = true;  // until a component is activated the grid stays that of the current state
+    // global minimum of Delta L (equals the minimum over the local minima)
+    MinLoc m{HUGE_VAL, 0x7fffffff};
+    for (int l = threadIdx.x; l < L; l += kNT) m = minloc(m, MinLoc{w.dl[l], l});
+    m = block_minloc<kNT>(m, sh->ml);
+    const double dlmin = m.v;
+    if (!(dlmin < 0.0)) return 0;
+    const double thr = dlmin / 5.0;
+    if (threadIdx.x == 0) sh->cand_count = 0;
+    __syncthreads();
+    for (int l = threadIdx.x; l < L; l += kNT) {
+      const double v = w.dl[l];
+      const double vl = w.dl[(l + L - 1) & (L - 1)], vr = w.dl[(l + 1) & (L - 1)];
+      if (v < vl && v <= vr && v <= thr) {
+        const int slot = atomicAdd(&sh->cand_count, 1);
+        w.cand[slot] = l;
+      }
+    }
+    __syncthreads();
+    const int nc = sh->cand_count;
+    __syncthreads();
+    int n_act = 0;
+    const double min_sep = 0.05 / (double)N;
+    for (int it = 0; it < nc; ++it) {
+      MinLoc b{HUGE_VAL, 0x7fffffff};
+      for (int j = threadIdx.x; j < nc; j += kNT) {
+        const int l = w.cand[j];
+        if (l >= 0) b = minloc(b, MinLoc{w.dl[l], l});
+      }
+      b = block_minloc<kNT>(b, sh->ml);
+      if (b.i == 0x7fffffff) break;
+      const int l = b.i;
+      // strike it out
+      for (int j = threadIdx.x; j < nc; j += kNT)
+        if (w.cand[j] == l) w.cand[j] = -1;
+      const double th = (double)l / (double)L;
+      int close = 0;
+      for (int k = threadIdx.x; k < sh->K; k += kNT) {
+        double d = fabs(th - w.theta[k]);
+        d = fmin(d, 1.0 - d);
+        close |= (d < min_sep);
+      }
+      close = __syncthreads_or(close);
+      if (threadIdx.x == 0 && !close && sh->K < N) {
+        double s;
+        c128 q;
+        grid_point(l, s, q);
+        const double aq2 = norm2(q);
+        const double ghat = aq2 > s ? (aq2 - s) / (s * s) : 0.0;
+        const double gb = K0 ? sh->gbar : ghat;
+        const double gs = gb * s;
+        const double rhs = (1.0 + 1.0 / gs) * (log1p(gs) + sh->lpo);
+        if (ghat > 0.0 && aq2 / s > rhs) {
+          w.theta[sh->K] = th;
+          w.gamma[sh->K] = ghat;
+          sh->K = sh->K + 1;
+        }
+      }
+      __syncthreads();
+    }
+    n_act = sh->K - K0;
+    if (n_act) {
+      grid_valid = false;
+      if (evaluate(w.theta, w.gamma, sh->K, true)) {
+        if (threadIdx.x == 0) sh->status = kST_NUMERIC;
+        __syncthreads();
+      }
+    }
+    return n_act;
+  }
+
+  // ------------------------------------------------------ Newton update ---
+  // Returns the squared Newton decrement.
+  __device__ double newton_iteration() {
+    const int K = sh->K;
+    const double inv_delta = 1.0 / sh->delta_last;
+    const double h_theta_fb = (50.0 * N) * (50.0 * N);
+    double dec = 0.0, slope = 0.0, amax = HUGE_VAL;
+    for (int k = threadIdx.x; k < K; k += kNT) {
+      const double g = w.gamma[k];
+      const CompVec cv = component_vectors<double>(w.sums + 7 * k, inv_delta);
+      const Derivs d = objective_derivatives(cv, g);
+      const double ht = d.ht > 0.0 ? d.ht : h_theta_fb;
+      const double hg = d.hg > 0.0 ? d.hg : 1.0 / (g * g);
+      const double dt = -d.gt / ht, dg = -d.gg / hg;
+      w.dth[k] = dt;
+      w.dga[k] = dg;
+      dec += d.gt * d.gt / ht + d.gg * d.gg / hg;
+      slope += d.gt * dt + d.gg * dg;
+      if (dg < 0.0) amax = fmin(amax, g / -dg);
+    }
+    dec = block_sum<kNT>(dec, sh->dred);
+    slope = block_sum<kNT>(slope, sh->dred);
+    MinLoc am{amax, 0};
+    am = block_minloc<kNT>(am, sh->ml);
+    if (dec < N * 1e-8) return dec;
+    double alpha = am.v < HUGE_VAL ? fmin(1.0, 0.99 * am.v) : 1.0;
+    const double f0 = sh->f_cur;
+    for (int j = 0; j < 31; ++j) {
+      for (int k = threadIdx.x; k < K; k += kNT) {
+        w.th_t[k] = mod1(w.theta[k] + alpha * w.dth[k]);
+        w.ga_t[k] = w.gamma[k] + alpha * w.dga[k];
+      }
+      __syncthreads();
+      const int bad = evaluate(w.th_t, w.ga_t, K, false);
+      if (!bad && sh->f_cur <= f0 + 1e-4 * alpha * slope) {
+        for (int k = threadIdx.x; k < K; k += kNT) {
+          w.theta[k] = w.th_t[k];
+          w.gamma[k] = w.ga_t[k];
+        }
+        __syncthreads();
+        compute_sums(K);
+        return dec;
+      }
+      alpha *= 0.5;
+    }
+    // no step accepted: restore the evaluation of the current state
+    if (evaluate(w.theta, w.gamma, K, true)) {
+      if (threadIdx.x == 0) sh->status = kST_NUMERIC;
+      __syncthreads();
+    }
+    return dec;
+  }
+
+  // ---------------------------------------------------------- deactivation ---
+  __device__ void deactivation() {
+    while (sh->K > 0 && sh->status == kST_OK) {
+      const int K = sh->K;
+      const double inv_delta = 1.0 / sh->delta_last;
+      const double thr = log_prior_odds(sh->zeta);
+      MinLoc m{HUGE_VAL, 0x7fffffff};
+      for (int k = threadIdx.x; k < K; k += kNT) {
+        const double g = w.gamma[k];
+        const CompVec cv = component_vectors<double>(w.sums + 7 * k, inv_delta);
+        const double den = 1.0 - g * cv.s;
+        const double st = cv.s / den;
+        const double aq2 = norm2(cv.q) / (den * den);
+        const double stat = g * aq2 / (1.0 + g * st) - log1p(g * st);
+        if (stat < thr) m = minloc(m, MinLoc{stat, k});
+      }
+      m = block_minloc<kNT>(m, sh->ml);
+      if (m.i == 0x7fffffff) break;
+      // stable removal of component m.i
+      double th = 0.0, ga = 0.0;
+      const int k = threadIdx.x;
+      for (int base = 0; base < K; base += kNT) {
+        const int kk = base + k;
+        if (kk >= m.i && kk + 1 < K) {
+          th = w.theta[kk + 1];
+          ga = w.gamma[kk + 1];
+        }
+        __syncthreads();
+        if (kk >= m.i && kk + 1 < K) {
+          w.theta[kk] = th;
+          w.gamma[kk] = ga;
+        }
+      }
+      if (threadIdx.x == 0) sh->K = K - 1;
+      __syncthreads();
+      if (evaluate(w.theta, w.gamma, sh->K, true)) {
+        if (threadIdx.x == 0) sh->status = kST_NUMERIC;
+        __syncthreads();
+      }
+    }
+  }
+
+  // ---------------------------------------------------------------- run ---
+  __device__ void run(int b) {
+    const InstDesc d = A->inst[b];
+    N = d.N;
+    L = d.L;
+    log2L = ilog2((uint32_t)L);
+    log2M2 = ilog2(2u * (uint32_t)N);
+    const float* yin = A->y + 2 * d.y_off;
+    double part = 0.0;
+    for (int n = threadIdx.x; n < N; n += kNT) {
+      const c128 v = mk((double)yin[2 * n], (double)yin[2 * n + 1]);
+      w.y[n] = v;
+      part += norm2(v);
+    }
+    const double yy = block_sum<kNT>(part, sh->dred);
+    // Levinson arrays in shared memory when they fit
+    int S, H;
+    first_column_split(N, S, H);
+    const size_t tab_bytes = sizeof(c128) * kFirstColumnChunk * (S + H);
+    lev_smem = (2 * sizeof(c128) * (size_t)N + tab_bytes) <= (size_t)kSmemBytes;
+    if (lev_smem) {
+      lev_c = (c128*)dsm;
+      lev_a = lev_c + N;
+      tables = lev_a + N;
+    } else {
+      lev_c = w.c;
+      lev_a = w.a;
+      tables = (c128*)dsm;
+    }
+    if (threadIdx.x == 0) {
+      sh->yy = yy;
+      sh->K = 0;
+      sh->status = kST_OK;
+      sh->n_evals = 0;
+      sh->n_grid = 0;
+      sh->beta = 0.01 * yy / N;
+      sh->eps_beta = 1e-12 * yy / N;
+      sh->zeta = 0.2;
+      sh->tau = A->cfg.tau;
+    }
+    __syncthreads();
+    FitOut o = A->out;
+    if (yy == 0.0) {  // degenerate: nothing to estimate
+      if (threadIdx.x == 0) {
+        o.K[b] = 0; o.beta[b] = 0.0; o.objective[b] = 0.0; o.iters[b] = 0; o.n_evals[b] = 0; o.n_grid[b] = 0;
+        o.status[b] = kST_OK;
+      }
+      __syncthreads();
+      return;
+    }
+    const c128* yv = w.y;
+    const int n_ = N;
+    block_fft<kNT, double>([=] __device__(int i) { return i < n_ ? yv[i] : zero<double>(); }, w.Yf, w.buf[4], log2M2,
+                           false, tw64);
+    int st = evaluate(w.theta, w.gamma, 0, true);
+    double L_prev = sh->f_cur - prior_term(0, N, sh->zeta);
+    bool approx = A->cfg.approx_iters > 0;
+    bool converged = false;
+    int it = 0;
+    if (st) {
+      if (threadIdx.x == 0) sh->status = kST_NUMERIC;
+      __syncthreads();
+    }
+    for (it = 1; it <= A->cfg.max_outer && sh->status == kST_OK; ++it) {
+      // step 1: activation
+      if (approx && it <= A->cfg.approx_iters) {
+        bool grid_valid;
+        const int n = approximate_activation(grid_valid);
+        if (n == 0) {
+          approx = false;
+          exact_activation(grid_valid);
+        }
+      } else {
+        exact_activation(false);
+      }
+      if (sh->status != kST_OK) break;
+      // step 2: zeta (eq. zetaUpdate)
+      // step 3: beta (eq. betaUpdate with the Woodbury forms of Sec. III-C3)
+      {
+        const int K = sh->K;
+        const double inv_delta = 1.0 / sh->delta_last;
+        double sg = 0.0, xx = 0.0;
+        for (int k = threadIdx.x; k < K; k += kNT) {
+          const c128* sm = w.sums + 7 * k;
+          const c128 r1r0 = sm[1] * conj(sm[0]);
+          sg += 2.0 * r1r0.re * inv_delta * w.gamma[k];
+        }
+        for (int n = threadIdx.x; n < N; n += kNT) xx += norm2(w.x[n]);
+        sg = block_sum<kNT>(sg, sh->dred);
+        xx = block_sum<kNT>(xx, sh->dred);
+        if (threadIdx.x == 0) {
+          sh->zeta = fmin(0.5, (double)K / (double)N);
+          const double b0 = sh->beta;
+          sh->beta = fmax(sh->eps_beta, (b0 * sg + b0 * b0 * xx) / N);
+        }
+        __syncthreads();
+        if (evaluate(w.theta, w.gamma, K, true)) {
+          if (threadIdx.x == 0) sh->status = kST_NUMERIC;
+          __syncthreads();
+          break;
+        }
+      }
+      // step 4
+      for (int inner = 0; inner < A->cfg.max_inner && sh->status == kST_OK; ++inner) {
+        if (sh->K == 0) break;
+        const double dec = newton_iteration();
+        deactivation();
+        if (dec < N * 1e-8) break;
+      }
+      if (sh->status != kST_OK) break;
+      const double L_cur = sh->f_cur - prior_term(sh->K, N, sh->zeta);
+      if (fabs(L_cur - L_prev) < N * 1e-7) {
+        converged = true;
+        break;
+      }
+      L_prev = L_cur;
+    }
+    // ------------------------------------------------------------ output --
+    const int K = sh->K;
+    const int64_t ro = d.y_off;
+    // rank sort by frequency (ties by index)
+    for (int k = threadIdx.x; k < K; k += kNT) {
+      const double t = w.theta[k];
+      int r = 0;
+      for (int j = 0; j < K; ++j) {
+        const double u = w.theta[j];
+        r += (u < t) || (u == t && j < k);
+      }
+      const double g = w.gamma[k];
+      const c128 q = w.sums[7 * k + 4];
+      o.theta[ro + r] = t;
+      o.gamma[ro + r] = g;
+      o.alpha[ro + r] = g * q;
+    }
+    if (threadIdx.x == 0) {
+      o.K[b] = K;
+      o.beta[b] = sh->beta;
+      o.objective[b] = sh->f_cur - prior_term(K, N, sh->zeta);
+      o.iters[b] = min(it, A->cfg.max_outer);
+      o.n_evals[b] = sh->n_evals;
+      o.n_grid[b] = sh->n_grid;
+      o.status[b] = sh->status != kST_OK ? sh->status : (converged ? kST_OK : kST_NOTCONV);
+    }
+    __syncthreads();
+  }
+};
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kNT, 1) fit_kernel(FitArgs args) {
+  using TG = typename Fitter<MIXED>::TG;
+  __shared__ FitShared sh;
+  extern __shared__ __align__(16) char dsm[];
+  Fitter<MIXED> F;
+  F.sh = &sh;
+  F.dsm = dsm;
+  F.A = &args;
+  F.w = carve<TG>(args.ws + (size_t)blockIdx.x * args.ws_bytes, args.Nmax, args.Lmax);
+  F.tw64 = Twiddles<double>{args.tab.tw64, args.tab.log2max};
+  if constexpr (MIXED) F.twg = Twiddles<TG>{(const cx<TG>*)args.tab.tw32, args.tab.log2max};
+  else F.twg = Twiddles<TG>{(const cx<TG>*)args.tab.tw64, args.tab.log2max};
+  for (;;) {
+    if (threadIdx.x == 0) sh.inst = atomicAdd(args.counter, 1);
+    __syncthreads();
+    const int b = sh.inst;
+    __syncthreads();
+    if (b >= args.B) break;
+    F.run(b);
+  }
+}
+
+}  // namespace
+
+size_t fit_workspace_bytes(int Nmax, int Lmax, bool mixed) {
+  return mixed ? make_layout<float>(Nmax, Lmax).total : make_layout<double>(Nmax, Lmax).total;
+}
+int fit_smem_bytes() { return kSmemBytes; }
+int fit_threads() { return kNT; }
+
+cudaError_t launch_fit(bool mixed, const float* y, const InstDesc* inst, int B, int Nmax, int Lmax,
+                       const FitConfig& cfg, const Tables& tab, const FitOut& out, void* ws, int* counter, int grid,
+                       cudaStream_t stream) {
+  FitArgs a;
+  a.y = y;
+  a.inst = inst;
+  a.B = B;
+  a.Nmax = Nmax;
+  a.Lmax = Lmax;
+  a.cfg = cfg;
+  a.tab = tab;
+  a.out = out;
+  a.ws = (char*)ws;
+  a.ws_bytes = fit_workspace_bytes(Nmax, Lmax, mixed);
+  a.counter = counter;
+  cudaError_t e;
+  if (mixed) {
+    e = cudaFuncSetAttribute(fit_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    fit_kernel<true><<<grid, kNT, kSmemBytes, stream>>>(a);
+  } else {
+    e = cudaFuncSetAttribute(fit_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    fit_kernel<false><<<grid, kNT, kSmemBytes, stream>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lse

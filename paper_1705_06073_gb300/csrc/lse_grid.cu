@@ -1,0 +1,193 @@
+// lse_grid.cu -- grid evaluation of Sec. IV-D (Hansen, Fleury, Rao,
+// "Superfast Line Spectral Estimation"): for a given state (theta, gamma,
+// beta) compute q(theta_l), s(theta_l) and their first and second
+// theta-derivatives at theta_l = l/L.
+//
+// Two kernels:
+//  factor_kernel  one block per instance: first column of C, Levinson
+//                 recursion (Gohberg-Semencul generators rho, delta) and
+//                 x = C^{-1} y by FFT convolutions (Sec. IV-A, IV-B).
+//  grid_kernel    the length-L spectra of index-weighted generators and the
+//                 pointwise combine.  With c = (N-2)/2 and
+//                   Q_a = DFT_L((n-c)^a rho_n),  X_a = DFT_L(n^a x_n)
+//                 the grid quantities are (Appendix B weights, centred)
+//                   s   = (2/d) Re(Q1 Q0*)
+//                   s'  = (4 pi/d) Im(Q2 Q0*)
+//                   s'' = (8 pi^2/d) [Re(Q2 Q1*) - Re(Q3 Q0*)]
+//                   q = X0,  q' = -j 2 pi X1,  q'' = -4 pi^2 X2
+//                 (d = delta_{N-1}; DFT_L(v)(l) = sum_n v_n e^{-j 2 pi n l / L}).
+#include "lse_device.cuh"
+#include "lse_internal.h"
+
+namespace lse {
+
+namespace {
+
+constexpr int kFNT = 256;
+
+struct FactorLayout {
+  size_t y, c, a, Yf, buf, total, M2;
+};
+__host__ __device__ inline FactorLayout factor_layout(int Nmax) {
+  FactorLayout L;
+  const size_t M2 = (size_t)1 << ilog2(2u * (uint32_t)Nmax);
+  size_t o = 0;
+  auto put = [&](size_t bytes) { size_t r = o; o += (bytes + 255) & ~size_t(255); return r; };
+  L.y = put(sizeof(c128) * Nmax);
+  L.c = put(sizeof(c128) * Nmax);
+  L.a = put(sizeof(c128) * Nmax);
+  L.Yf = put(sizeof(c128) * M2);
+  L.buf = put(sizeof(c128) * M2 * 5);
+  L.total = o;
+  L.M2 = M2;
+  return L;
+}
+
+__global__ void __launch_bounds__(kFNT, 1)
+    factor_kernel(const float* y, const InstDesc* inst, int Nmax, const double* theta, const double* gamma,
+                  const double* beta, Tables tab, char* ws, size_t ws_bytes, c128* rho_out, c128* x_out,
+                  double* delta_out, int* status) {
+  __shared__ c128 red[kFNT];
+  __shared__ double dred[kFNT / 32];
+  __shared__ LevShared lev;
+  extern __shared__ __align__(16) char dsm[];
+  const int b = blockIdx.x;
+  const InstDesc d = inst[b];
+  const int N = d.N;
+  char* base = ws + (size_t)b * ws_bytes;
+  const FactorLayout FL = factor_layout(Nmax);
+  c128* yv = (c128*)(base + FL.y);
+  c128* Yf = (c128*)(base + FL.Yf);
+  c128* bufp = (c128*)(base + FL.buf);
+  c128* bufs[5];
+  for (int j = 0; j < 5; ++j) bufs[j] = bufp + (size_t)j * FL.M2;
+  const Twiddles<double> tw{tab.tw64, tab.log2max};
+  const int log2M2 = ilog2(2u * (uint32_t)N);
+  const float* yin = y + 2 * d.y_off;
+  for (int n = threadIdx.x; n < N; n += kFNT) yv[n] = mk((double)yin[2 * n], (double)yin[2 * n + 1]);
+  __syncthreads();
+  int S, H;
+  first_column_split(N, S, H);
+  const size_t tab_bytes = sizeof(c128) * kFirstColumnChunk * (S + H);
+  const int smem_cap = 200 * 1024;
+  c128 *cc, *aa, *tables;
+  if (2 * sizeof(c128) * (size_t)N + tab_bytes <= (size_t)smem_cap) {
+    cc = (c128*)dsm; aa = cc + N; tables = aa + N;
+  } else {
+    cc = (c128*)(base + FL.c); aa = (c128*)(base + FL.a); tables = (c128*)dsm;
+  }
+  block_first_column<kFNT>(cc, theta + d.k_off, gamma + d.k_off, d.K, beta[b], N, tables);
+  const LevResult lr = block_levinson<kFNT>(cc, aa, N, red, &lev);
+  c128* rho = rho_out + d.y_off;
+  c128* x = x_out + d.y_off;
+  if (lr.status) {
+    if (threadIdx.x == 0) { status[b] = 4; delta_out[b] = 0.0; }
+    for (int n = threadIdx.x; n < N; n += kFNT) { rho[n] = zero<double>(); x[n] = zero<double>(); }
+    return;
+  }
+  for (int n = threadIdx.x; n < N; n += kFNT) rho[n] = conj(aa[N - 1 - n]);
+  block_fft<kFNT, double>([=] __device__(int i) { return i < N ? yv[i] : zero<double>(); }, Yf, bufs[4], log2M2, false,
+                          tw);
+  block_gs_apply<kFNT>(rho, Yf, x, N, log2M2, lr.delta_last, bufs, tw);
+  (void)dred;
+  if (threadIdx.x == 0) { status[b] = 0; delta_out[b] = lr.delta_last; }
+}
+
+// ------------------------------------------------------------------ grid ---
+// One block per (instance, family): family 0 makes s, s', s'' from Q0..Q3,
+// family 1 makes q, q', q'' from X0..X2.  Spectra are built with the block
+// FFT in the workspace (L2-resident) and combined pointwise.
+template <class T>
+__global__ void __launch_bounds__(kFNT, 1)
+    grid_kernel(const InstDesc* inst, const c128* rho_all, const c128* x_all, const double* delta, Tables tab,
+                char* ws, const int64_t* ws_off, T* q, T* dq, T* d2q, T* s, T* ds, T* d2s) {
+  const int b = blockIdx.x >> 1, fam = blockIdx.x & 1;
+  const InstDesc d = inst[b];
+  const int N = d.N, L = d.L, log2L = ilog2((uint32_t)L);
+  const Twiddles<T> tw{(const cx<T>*)(sizeof(T) == 8 ? (const void*)tab.tw64 : (const void*)tab.tw32), tab.log2max};
+  cx<T>* buf = (cx<T>*)(ws + ws_off[b] + (size_t)fam * 5 * L * sizeof(cx<T>));
+  cx<T>* B[5];
+  for (int j = 0; j < 5; ++j) B[j] = buf + (size_t)j * L;
+  const int64_t g = d.g_off;
+  if (fam == 0) {
+    const c128* rho = rho_all + d.y_off;
+    const double cen = 0.5 * (double)(N - 2);
+    const double inv_d = 1.0 / delta[b];
+    for (int a = 0; a < 4; ++a) {
+      block_fft<kFNT, T>(
+          [=] __device__(int i) {
+            if (i >= N) return zero<T>();
+            const double w = (double)i - cen;
+            double p = 1.0;
+            for (int e = 0; e < a; ++e) p *= w;
+            return cvt<T>(p * rho[i]);
+          },
+          B[a], B[4], log2L, false, tw);
+    }
+    for (int l = threadIdx.x; l < L; l += kFNT) {
+      const cx<T> Q0 = B[0][l], Q1 = B[1][l], Q2 = B[2][l], Q3 = B[3][l];
+      const cx<T> q10 = Q1 * conj(Q0), q20 = Q2 * conj(Q0), q21 = Q2 * conj(Q1), q30 = Q3 * conj(Q0);
+      if (s) s[g + l] = (T)(2.0 * inv_d) * q10.re;
+      if (ds) ds[g + l] = (T)(4.0 * kPi * inv_d) * q20.im;
+      if (d2s) d2s[g + l] = (T)(8.0 * kPi * kPi * inv_d) * (q21.re - q30.re);
+    }
+  } else {
+    const c128* x = x_all + d.y_off;
+    for (int a = 0; a < 3; ++a) {
+      block_fft<kFNT, T>(
+          [=] __device__(int i) {
+            if (i >= N) return zero<T>();
+            double p = 1.0;
+            for (int e = 0; e < a; ++e) p *= (double)i;
+            return cvt<T>(p * x[i]);
+          },
+          B[a], B[4], log2L, false, tw);
+    }
+    cx<T>* Q = (cx<T>*)q;
+    cx<T>* DQ = (cx<T>*)dq;
+    cx<T>* D2Q = (cx<T>*)d2q;
+    for (int l = threadIdx.x; l < L; l += kFNT) {
+      if (Q) Q[g + l] = B[0][l];
+      if (DQ) DQ[g + l] = (T)(-kTwoPi) * mul_j(B[1][l]);
+      if (D2Q) D2Q[g + l] = (T)(-4.0 * kPi * kPi) * B[2][l];
+    }
+  }
+}
+
+}  // namespace
+
+size_t factor_workspace_bytes(int Nmax) { return factor_layout(Nmax).total; }
+
+cudaError_t launch_factor(const float* y, const InstDesc* inst, int B, int Nmax, const double* theta,
+                          const double* gamma, const double* beta, const Tables& tab, void* ws, c128* rho_out,
+                          c128* x_out, double* delta_out, int* status, cudaStream_t stream) {
+  const int smem = 200 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  factor_kernel<<<B, kFNT, smem, stream>>>(y, inst, Nmax, theta, gamma, beta, tab, (char*)ws,
+                                           factor_workspace_bytes(Nmax), rho_out, x_out, delta_out, status);
+  return cudaGetLastError();
+}
+
+size_t grid_workspace_bytes(int B, int64_t total_L, bool f32) {
+  (void)B;
+  return (size_t)total_L * 2 * 5 * (f32 ? sizeof(c64) : sizeof(c128));
+}
+
+cudaError_t launch_grid(bool f32, const InstDesc* inst, int B, int Lmax, const c128* rho, const c128* x,
+                        const double* delta, const Tables& tab, void* ws, void* q, void* dq, void* d2q, void* s,
+                        void* ds, void* d2s, cudaStream_t stream) {
+  (void)Lmax;
+  // ws begins with B int64 offsets (per instance, bytes) followed by buffers
+  const int64_t* ws_off = (const int64_t*)ws;
+  char* base = (char*)ws;
+  if (f32)
+    grid_kernel<float><<<2 * B, kFNT, 0, stream>>>(inst, rho, x, delta, tab, base, ws_off, (float*)q, (float*)dq,
+                                                   (float*)d2q, (float*)s, (float*)ds, (float*)d2s);
+  else
+    grid_kernel<double><<<2 * B, kFNT, 0, stream>>>(inst, rho, x, delta, tab, base, ws_off, (double*)q, (double*)dq,
+                                                    (double*)d2q, (double*)s, (double*)ds, (double*)d2s);
+  return cudaGetLastError();
+}
+
+}  // namespace lse

@@ -1,0 +1,71 @@
+// lse_internal.h -- host-side declarations shared by the translation units of
+// the library (not part of the public ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lse_common.cuh"
+
+namespace lse {
+
+// One instance of a batched launch.
+struct InstDesc {
+  int64_t y_off;   // offset of y (complex elements) in the batch
+  int32_t N;
+  int32_t L;       // grid size (power of two >= 2N)
+  int64_t k_off;   // eval-grid: offset of this instance's components; fit: unused
+  int32_t K;       // eval-grid: number of components
+  int32_t pad;
+  int64_t g_off;   // eval-grid: offset of this instance's grid outputs
+};
+
+struct FitConfig {
+  double tau;
+  int max_outer, max_inner, approx_iters;
+};
+
+// Device outputs of the fit kernel (see lse_batch_out).
+struct FitOut {
+  double* theta;
+  double* gamma;
+  c128* alpha;
+  int* K;
+  double* beta;
+  double* objective;
+  int* iters;
+  int* n_evals;
+  int* n_grid;
+  int* status;
+};
+
+struct Tables {
+  const c128* tw64;
+  const c64* tw32;
+  int log2max;
+};
+
+// Per-CTA workspace needed by the fit kernel for instances up to (Nmax, Lmax).
+size_t fit_workspace_bytes(int Nmax, int Lmax, bool mixed);
+int fit_smem_bytes();
+int fit_threads();
+
+// Launch the persistent fit kernel over B instances on `stream` with `grid`
+// CTAs; `ws` holds grid * fit_workspace_bytes(Nmax, Lmax, mixed) bytes and
+// `counter` one zeroed int (work queue).
+cudaError_t launch_fit(bool mixed, const float* y, const InstDesc* inst, int B, int Nmax, int Lmax, const FitConfig& cfg,
+                       const Tables& tab, const FitOut& out, void* ws, int* counter, int grid, cudaStream_t stream);
+
+// Eval-grid: per-instance factorisation (first column, Levinson, GS apply).
+size_t factor_workspace_bytes(int Nmax);
+cudaError_t launch_factor(const float* y, const InstDesc* inst, int B, int Nmax, const double* theta,
+                          const double* gamma, const double* beta, const Tables& tab, void* ws, c128* rho_out,
+                          c128* x_out, double* delta_out, int* status, cudaStream_t stream);
+// Eval-grid: spectra and combine.  outputs in T (float for mixed, double for fp64).
+cudaError_t launch_grid(bool f32, const InstDesc* inst, int B, int Lmax, const c128* rho, const c128* x,
+                        const double* delta, const Tables& tab, void* ws, void* q, void* dq, void* d2q, void* s,
+                        void* ds, void* d2s, cudaStream_t stream);
+size_t grid_workspace_bytes(int B, int64_t total_L, bool f32);
+
+}  // namespace lse

@@ -1,0 +1,105 @@
+"""Whole fits on the GPU through the C ABI against the oracle's fits.
+
+Bar: equal K and every frequency within 1e-6 cycles (wrap distance) of the
+oracle's; gamma, beta and the objective agree to the precision the path
+carries (FP64: 1e-6 relative).
+"""
+import numpy as np
+import pytest
+
+from oracle import fit as ofit
+from paper_1705_06073_gb300 import synth
+from tests.gpu_util import match_fit, wrapdist
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lse_mod():
+    from paper_1705_06073_gb300 import build, lse
+    build.build()
+    return lse
+
+
+def make_ctx(lse, L=0, **kw):
+    return lse.lse_create(lse.lse_config_default(grid_size=L, **kw))
+
+
+def check(gpu, ref, tol_theta=1e-6, tol_rel=1e-6):
+    assert match_fit(gpu, ref) < tol_theta
+    if ref.K:
+        assert np.allclose(gpu["gamma"], ref.gamma, rtol=tol_rel)
+        assert np.allclose(gpu["alpha"], ref.alpha, rtol=tol_rel, atol=tol_rel * np.abs(ref.alpha).max())
+    assert abs(gpu["beta"] - ref.beta) <= tol_rel * ref.beta
+    assert abs(gpu["objective"] - ref.objective) <= tol_rel * max(1.0, abs(ref.objective))
+
+
+def test_fit_single_n256(lse_mod):
+    inst, L = synth.single_n256()[0]
+    ctx = make_ctx(lse_mod, L)
+    try:
+        gpu = lse_mod.lse_fit(ctx, inst.y)
+    finally:
+        lse_mod.lse_destroy(ctx)
+    ref = ofit.fit(inst.y, L)
+    check(gpu, ref)
+    assert gpu["iters"] == ref.iters
+    assert gpu["n_evals"] == ref.n_evals
+    assert gpu["n_grid"] == ref.n_grid_evals
+
+
+@pytest.mark.parametrize("N,K,snr,seed", [(64, 3, 25.0, 1), (100, 4, 15.0, 2), (128, 10, 20.0, 3), (37, 2, 30.0, 4),
+                                          (200, 6, 10.0, 5)])
+def test_fit_small_instances(lse_mod, N, K, snr, seed):
+    inst = synth.make_instance(N, K, snr, 7000 + seed)
+    L = synth.default_grid_size(N)
+    ctx = make_ctx(lse_mod)
+    try:
+        gpu = lse_mod.lse_fit(ctx, inst.y)
+    finally:
+        lse_mod.lse_destroy(ctx)
+    ref = ofit.fit(inst.y, L)
+    check(gpu, ref)
+
+
+def test_fit_batch_ragged_matches_single_fits(lse_mod):
+    """One launch over instances of different N; each equals the oracle's fit."""
+    specs = [(48, 2), (130, 5), (77, 3), (256, 8), (33, 1), (160, 4)]
+    insts = [synth.make_instance(N, K, 20.0, 8000 + i) for i, (N, K) in enumerate(specs)]
+    ctx = make_ctx(lse_mod)
+    try:
+        res = lse_mod.lse_fit_batch(ctx, [i.y for i in insts])
+    finally:
+        lse_mod.lse_destroy(ctx)
+    for inst, gpu in zip(insts, res):
+        ref = ofit.fit(inst.y, synth.default_grid_size(inst.N))
+        check(gpu, ref)
+
+
+def test_fit_degenerate_inputs(lse_mod):
+    ctx = make_ctx(lse_mod)
+    try:
+        r = lse_mod.lse_fit(ctx, np.zeros(16, np.complex64))
+        assert r["K"] == 0 and r["beta"] == 0.0
+        # pure noise: the oracle decides; typically nothing is activated
+        y = synth.Stream(5).cnormal(32).astype(np.complex64)
+        gpu = lse_mod.lse_fit(ctx, y)
+        check(gpu, ofit.fit(y, synth.default_grid_size(32)))
+        # smallest N
+        y2 = np.array([1 + 1j, 0.5 - 0.2j], np.complex64)
+        gpu = lse_mod.lse_fit(ctx, y2)
+        check(gpu, ofit.fit(y2, synth.default_grid_size(2)))
+        with pytest.raises(lse_mod.LseError):
+            lse_mod.lse_fit(ctx, np.ones(1, np.complex64))
+    finally:
+        lse_mod.lse_destroy(ctx)
+
+
+def test_fit_capacity_error(lse_mod):
+    inst, L = synth.single_n256()[0]
+    ctx = make_ctx(lse_mod, L)
+    try:
+        r = lse_mod.lse_fit_batch(ctx, [inst.y], K_cap=2)[0]
+        assert r["status"] == lse_mod.LSE_ECAPACITY and r["K"] == 8 and r["theta"] is None
+    finally:
+        lse_mod.lse_destroy(ctx)

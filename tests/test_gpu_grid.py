@@ -1,0 +1,109 @@
+"""GPU grid evaluation (Sec. IV-D) through the C ABI against the dense FP64
+oracle, element by element.
+
+Tolerances: FP64 path 1e-8 normwise (and 1e-8 pointwise for s): the
+Levinson recursion and FFT convolutions lose about kappa(C) * 1e-16, and the
+states here have kappa(C) <= 1e6.  Mixed path (FP32 spectra): 1e-4
+normwise, the bound the hot path is specified to meet.
+"""
+import numpy as np
+import pytest
+
+from oracle import dense as dn
+from paper_1705_06073_gb300 import synth
+from tests.gpu_util import grid_errors
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("q", "dq", "d2q", "s", "ds", "d2s")
+
+
+@pytest.fixture(scope="module")
+def ctxs():
+    from paper_1705_06073_gb300 import build, lse
+    build.build()
+    c64 = lse.lse_create(lse.lse_config_default(precision=lse.LSE_PREC_FP64))
+    cmx = lse.lse_create(lse.lse_config_default(precision=lse.LSE_PREC_MIXED))
+    yield c64, cmx
+    lse.lse_destroy(c64)
+    lse.lse_destroy(cmx)
+
+
+def state(N, K, seed):
+    inst = synth.make_instance(N, K, 20.0, seed) if K else synth.make_instance(N, 0, 20.0, seed)
+    r = np.random.default_rng(seed)
+    gamma = np.abs(inst.alpha) ** 2 + 0.05 if K else np.zeros(0)
+    theta = np.mod(inst.theta + 1e-3 * r.standard_normal(K), 1.0) if K else np.zeros(0)
+    beta = inst.beta if K else 0.3
+    return inst.y, theta, gamma, beta
+
+
+CASES = [(2, 0, 4), (2, 1, 4), (7, 2, 16), (16, 1, 32), (33, 3, 128), (64, 4, 128), (100, 5, 256),
+         (256, 8, 2048), (300, 12, 1024), (512, 16, 1024)]
+
+
+@pytest.mark.parametrize("N,K,L", CASES)
+def test_grid_fp64_matches_oracle(ctxs, N, K, L):
+    from paper_1705_06073_gb300 import lse
+    y, th, ga, be = state(N, K, 1000 + N)
+    got = lse.lse_eval_grid(ctxs[0], y, th, ga, be, L, f64=True)
+    ref = dn.DenseEval(y, th, ga, be).grid(L, derivatives=True)
+    err = grid_errors(got, ref, N)
+    assert max(err.values()) < 1e-8, err
+    assert np.all(np.abs(got["s"] - ref["s"]) <= 1e-8 * ref["s"])
+
+
+@pytest.mark.parametrize("N,K,L", CASES)
+def test_grid_mixed_matches_oracle(ctxs, N, K, L):
+    from paper_1705_06073_gb300 import lse
+    y, th, ga, be = state(N, K, 2000 + N)
+    got = lse.lse_eval_grid(ctxs[1], y, th, ga, be, L, f64=False)
+    ref = dn.DenseEval(y, th, ga, be).grid(L, derivatives=True)
+    err = grid_errors(got, ref, N)
+    assert max(err.values()) < 1e-4, err
+
+
+def test_grid_batch_ragged_device(ctxs):
+    """Several instances of different N, K and L in one batched launch, each
+    against the oracle."""
+    import torch
+    from paper_1705_06073_gb300 import lse
+    specs = [(37, 2, 128), (128, 0, 256), (250, 6, 512), (64, 3, 512)]
+    ys, ths, gas, bes = [], [], [], []
+    for i, (N, K, L) in enumerate(specs):
+        y, th, ga, be = state(N, K, 3000 + i)
+        ys.append(y); ths.append(th); gas.append(ga); bes.append(be)
+    yo = np.concatenate([[0], np.cumsum([len(y) for y in ys])])
+    ko = np.concatenate([[0], np.cumsum([len(t) for t in ths])])
+    Ls = np.array([s[2] for s in specs], np.int32)
+    dev = torch.device("cuda:0")
+    y_d = torch.from_numpy(np.concatenate(ys)).to(dev)
+    th_d = torch.from_numpy(np.concatenate(ths + [np.zeros(1)])).to(dev)
+    ga_d = torch.from_numpy(np.concatenate(gas + [np.zeros(1)])).to(dev)
+    be_d = torch.tensor(bes, dtype=torch.float64, device=dev)
+    G = int(Ls.sum())
+    outs = {f: torch.zeros(G, dtype=torch.complex128 if f in ("q", "dq", "d2q") else torch.float64, device=dev)
+            for f in FIELDS}
+    lse.lse_eval_grid_batch_d(ctxs[0], y_d, yo, th_d, ga_d, ko, be_d, Ls, outs, f64=True)
+    torch.cuda.synchronize()
+    g0 = 0
+    for i, (N, K, L) in enumerate(specs):
+        ref = dn.DenseEval(ys[i], ths[i], gas[i], bes[i]).grid(L, derivatives=True)
+        got = {f: outs[f][g0:g0 + L].cpu().numpy() for f in FIELDS}
+        err = grid_errors(got, ref, N)
+        assert max(err.values()) < 1e-8, (i, err)
+        g0 += L
+
+
+def test_grid_rejects_bad_arguments(ctxs):
+    from paper_1705_06073_gb300 import lse
+    y = np.ones(8, np.complex64)
+    with pytest.raises(lse.LseError) as e:
+        lse.lse_eval_grid(ctxs[0], y, [], [], 1.0, 12, f64=True)  # L not a power of two
+    assert e.value.status == lse.LSE_EINVAL
+    with pytest.raises(lse.LseError):
+        lse.lse_eval_grid(ctxs[0], y, [], [], 1.0, 8, f64=True)  # L < 2N
+    with pytest.raises(lse.LseError):
+        lse.lse_eval_grid(ctxs[0], y, [], [], 0.0, 16, f64=True)  # beta <= 0
+    with pytest.raises(lse.LseError):
+        lse.lse_eval_grid(ctxs[0], y, [], [], 1.0, 16, f64=False)  # dtype mismatch
