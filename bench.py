@@ -177,7 +177,7 @@ def run_reference(args, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "fitted instances/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median([x["wall"] for x in vals]),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "B": B, "N": N, "K": K, "L": L, "l2": "n/a (CPU)"},
+            "config": {"workload": WORKLOAD if Bn == B else f"batch{Bn}_n4096_k64_l16384", "B": Bn, "N": N, "K": K, "L": L, "l2": "n/a (CPU)"},
             "cpu_baseline": desc,
             "e2e": {"value": v, "unit": "fitted instances/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -192,6 +192,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--batch", type=int, default=B, help="instances per step (smaller cases for profiling)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-API end-to-end leg")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -216,7 +218,8 @@ def main():
     __graft_entry__.build()
     from paper_1705_06073_gb300 import lse, synth
 
-    insts = synth.batch64_n4096(seed0=201 + 100000 * rank, B=B)
+    Bn = args.batch
+    insts = synth.batch64_n4096(seed0=201 + 100000 * rank, B=Bn)
     ys = [i.y for i, _ in insts]
     offsets = np.concatenate([[0], np.cumsum([len(y) for y in ys])]).astype(np.int64)
     y_host = np.ascontiguousarray(np.concatenate(ys))
@@ -284,7 +287,7 @@ def main():
         total_ms = max_over_ranks(sum(ms))
         res[name] = dict(ms=ms, total_ms=total_ms, kernel_ms=kms / max(launches, 1), launches=launches,
                          n_evals=n_ev, n_grid=n_gr, status=st, K=Kf,
-                         value=sum_over_ranks(B * args.steps) / (total_ms / 1e3), out=out)
+                         value=sum_over_ranks(Bn * args.steps) / (total_ms / 1e3), out=out)
 
     # ---- grid-point throughput at the fitted states (factor + grid kernels)
     grid = {}
@@ -293,21 +296,21 @@ def main():
         out = res[name]["out"]
         f64 = name == "fp64"
         Ks = out["K"].cpu().numpy().astype(np.int64)
-        ko = np.zeros(B + 1, np.int64)
+        ko = np.zeros(Bn + 1, np.int64)
         th_l, ga_l = [], []
         th_all = out["theta"].cpu().numpy()
         ga_all = out["gamma"].cpu().numpy()
-        for b in range(B):
+        for b in range(Bn):
             th_l.append(th_all[offsets[b]:offsets[b] + Ks[b]])
             ga_l.append(ga_all[offsets[b]:offsets[b] + Ks[b]])
             ko[b + 1] = ko[b] + Ks[b]
         th_d = torch.from_numpy(np.concatenate(th_l + [np.zeros(1)])).to(dev)
         ga_d = torch.from_numpy(np.concatenate(ga_l + [np.zeros(1)])).to(dev)
         be_d = out["beta"].clone()
-        Ls = np.full(B, L, np.int32)
+        Ls = np.full(Bn, L, np.int32)
         ct = torch.complex128 if f64 else torch.complex64
         rt = torch.float64 if f64 else torch.float32
-        outs = {f: torch.empty(B * L, dtype=ct if f in ("q", "dq", "d2q") else rt, device=dev)
+        outs = {f: torch.empty(Bn * L, dtype=ct if f in ("q", "dq", "d2q") else rt, device=dev)
                 for f in ("q", "dq", "d2q", "s", "ds", "d2s")}
         for _ in range(args.warmup):
             lse.lse_eval_grid_batch_d(ctx, y_d, offsets, th_d, ga_d, ko, be_d, Ls, outs, f64, stream)
@@ -330,22 +333,23 @@ def main():
         fms, fl = lse.lse_kernel_time(ctx, 1)
         gms, gl = lse.lse_kernel_time(ctx, 2)
         tot = max_over_ranks(sum(ms))
-        grid[name] = dict(value=sum_over_ranks(B * L * args.steps) / (tot / 1e3), ms=tot / args.steps,
+        grid[name] = dict(value=sum_over_ranks(Bn * L * args.steps) / (tot / 1e3), ms=tot / args.steps,
                           factor_ms=fms / max(fl, 1), grid_ms=gms / max(gl, 1), launches=fl + gl)
 
     # ---- end to end through the host API (pinned host inputs, results back)
     ctx = ctxs["mixed"]
-    lse.lse_fit_batch(ctx, ys)  # warm the staging buffers
+    if not args.no_e2e:
+        lse.lse_fit_batch(ctx, ys)  # warm the staging buffers
     e2e_ms = []
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(0 if args.no_e2e else max(1, min(args.steps, 3))):
         barrier()
         t0 = time.perf_counter()
         lse.lse_fit_batch(ctx, ys)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_tot = max_over_ranks(sum(e2e_ms))
-    e2e_val = sum_over_ranks(B * len(e2e_ms)) / (e2e_tot / 1e3)
+    e2e_val = sum_over_ranks(Bn * len(e2e_ms)) / (e2e_tot / 1e3) if e2e_ms else None
     h2d = int(y_host.nbytes)  # y (complex64)
-    d2h = int(offsets[-1] * (8 + 8 + 16) + B * (8 + 8 + 4 * 5))  # theta, gamma, alpha slices + per-instance scalars
+    d2h = int(offsets[-1] * (8 + 8 + 16) + Bn * (8 + 8 + 4 * 5))  # theta, gamma, alpha slices + per-instance scalars
 
     for c in ctxs.values():
         lse.lse_destroy(c)
@@ -380,7 +384,7 @@ def main():
         "vs_baseline": None,
         "dtype": "f64 recursion + f32 grid/sums (mixed)",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "B": B, "N": N, "K": K, "L": L, "snr_db": "U[10,30]",
+        "config": {"workload": WORKLOAD if Bn == B else f"batch{Bn}_n4096_k64_l16384", "B": Bn, "N": N, "K": K, "L": L, "snr_db": "U[10,30]",
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"instances sharded x{world}"},
         "clocks": clocks,
         "gpu_launches": int(m["launches"]),
@@ -394,7 +398,7 @@ def main():
                 "status_nonzero": int(np.count_nonzero(m["status"])), "fit_kernel_ms": m["kernel_ms"]},
         "grid_pt_evals": {"value": gm["value"], "unit": "grid-pt evals/s", "ms_per_batch": gm["ms"],
                           "factor_kernel_ms": gm["factor_ms"], "grid_kernel_ms": gm["grid_ms"],
-                          "grid_kernel_hbm_gbs": B * grid_bytes(N, L, False) / (gm["grid_ms"] / 1e3) / 1e9},
+                          "grid_kernel_hbm_gbs": Bn * grid_bytes(N, L, False) / (gm["grid_ms"] / 1e3) / 1e9},
         "cpu_baseline": cpu,
     }
     if "fp64" in res:
@@ -404,7 +408,7 @@ def main():
                              "fit_kernel_ms": f["kernel_ms"], "n_evals_mean": float(np.mean(f["n_evals"])),
                              "grid_pt_evals": gf["value"], "grid_kernel_ms": gf["grid_ms"],
                              "factor_kernel_ms": gf["factor_ms"],
-                             "grid_kernel_hbm_gbs": B * grid_bytes(N, L, True) / (gf["grid_ms"] / 1e3) / 1e9}
+                             "grid_kernel_hbm_gbs": Bn * grid_bytes(N, L, True) / (gf["grid_ms"] / 1e3) / 1e9}
         line["mixed_over_fp64"] = {"fit": m["value"] / f["value"], "grid": gm["value"] / gf["value"]}
     print(json.dumps(line), flush=True)
     if dist:
