@@ -185,6 +185,43 @@ LSE_API lse_status lse_eval_grid_batch_d(lse_ctx* ctx, const float* y_d, const i
  * clears the record. */
 LSE_API lse_status lse_kernel_time(lse_ctx* ctx, int32_t which, double* total_ms, int64_t* launches);
 
+/* Fit one instance without allocating any device memory.
+ *
+ * For callers that must not allocate on the GPU when they run a fit: loops
+ * with a hard per-frame deadline (cudaMalloc/cudaFree can stall for
+ * milliseconds and synchronise the whole device), hosts embedded in a
+ * framework that owns every device allocation, or code that has finished
+ * its set-up phase and may no longer call the allocator.  No context is
+ * needed; nothing here calls cudaMalloc, cudaFree or any allocating routine.
+ *
+ * The paper has no counterpart to this entry point.
+ *
+ * The caller passes y_d (device complex64 [2N floats]) and out: device
+ * arrays as in lse_batch_out for B = 1 (theta, gamma capacity N, alpha 2N
+ * doubles, and one element each for K, beta, objective, iters, n_evals,
+ * n_grid, status).  cfg (host, may be NULL for the defaults) supplies tau,
+ * the iteration limits, grid_size and precision; cfg->device and
+ * hbm_budget_bytes are ignored -- the fit runs on the current device.
+ * The fit is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ * stream) and the call returns without waiting.
+ *
+ * Limits: 2 <= N <= 4096 and L <= 32768 (L = cfg->grid_size, or 8N rounded
+ * to the nearest power of two), and the kernel workspace for (N, L) must fit
+ * the library's 8 MiB static scratch array; anything larger returns
+ * LSE_EINVAL before any work is enqueued.
+ *
+ * The scratch is a fixed array inside the library, present on every GPU
+ * that loads it until the process exits, and shared by all calls: calls
+ * whose work overlaps on the GPU (other streams, other host threads) race
+ * on it, so serialise them.  Each call clears what must start at zero (the
+ * launch's work counter); the rest keeps the previous call's contents and
+ * is rewritten before it is read.  The first call on a device does a
+ * one-time set-up there (looking up the device addresses of the static
+ * arrays and filling a twiddle table); make that first call before any
+ * stream capture. */
+LSE_API lse_status lse_fit_noalloc_d(const lse_config* cfg, const float* y_d, int32_t N,
+                                     const lse_batch_out* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -253,3 +253,21 @@ def lse_kernel_time(ctx, which: int):
     n = ctypes.c_int64()
     _check(ctx, load().lse_kernel_time(ctx, which, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def lse_fit_noalloc_d(y_d, N: int, out: dict, cfg: lse_config | None = None, stream=None) -> None:
+    """Single-instance fit that allocates no device memory (see include/lse.h):
+    y_d a torch complex64 CUDA tensor, out a dict of torch CUDA tensors as
+    from alloc_batch_out for one instance of size N."""
+    lib = load()
+    f = lib.lse_fit_noalloc_d
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.POINTER(lse_config), ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(lse_batch_out),
+                  ctypes.c_void_p]
+    bo = lse_batch_out(out["theta"].data_ptr(), out["gamma"].data_ptr(), out["alpha"].data_ptr(),
+                       out["K"].data_ptr(), out["beta"].data_ptr(), out["objective"].data_ptr(),
+                       out["iters"].data_ptr(), out["n_evals"].data_ptr(), out["n_grid"].data_ptr(),
+                       out["status"].data_ptr())
+    s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    st = f(ctypes.byref(cfg) if cfg is not None else None, ctypes.c_void_p(y_d.data_ptr()), int(N), ctypes.byref(bo), s)
+    _check(None, st)
