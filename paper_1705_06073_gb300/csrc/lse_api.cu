@@ -190,7 +190,8 @@ lse_status lse_create(const lse_config* cfg, lse_ctx** out) {
   *out = nullptr;
   lse_config c;
   if (cfg) c = *cfg; else lse_config_default(&c);
-  if (c.precision != LSE_PREC_FP64 && c.precision != LSE_PREC_MIXED) return LSE_EINVAL;
+  if (c.precision != LSE_PREC_FP64 && c.precision != LSE_PREC_MIXED && c.precision != LSE_PREC_MIXED_DF)
+    return LSE_EINVAL;
   if (c.max_outer < 1 || c.max_inner < 0 || c.approx_activation_iters < 0 || !(c.tau >= 0.0) || c.flags)
     return LSE_EINVAL;
   if (c.grid_size < 0 || (c.grid_size > 0 && !is_pow2(c.grid_size))) return LSE_EINVAL;
@@ -266,11 +267,11 @@ lse_status lse_fit_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* offset
     Nmax = std::max(Nmax, N);
     Lmax = std::max(Lmax, L);
   }
-  const bool mixed = ctx->cfg.precision == LSE_PREC_MIXED;
+  const int prec = ctx->cfg.precision;
   lse_status s = ensure_tables(ctx, std::max(ilog2((uint32_t)Lmax), ilog2(2u * (uint32_t)Nmax)));
   if (s) return s;
   const int grid = std::min(B, ctx->sm_count);
-  const size_t per = fit_workspace_bytes(Nmax, Lmax, mixed);
+  const size_t per = fit_workspace_bytes(Nmax, Lmax, prec);
   if ((s = ensure(ctx, ctx->ws, per * grid))) return s;
   if ((s = stage_desc(ctx, d))) return s;
   if (st != ctx->stream) {
@@ -285,7 +286,7 @@ lse_status lse_fit_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* offset
   FitOut fo{out->theta, out->gamma, (c128*)out->alpha, out->K, out->beta, out->objective, out->iters,
             out->n_evals, out->n_grid, out->status};
   record(ctx, 0, st, true);
-  cudaError_t e = launch_fit(mixed, y_d, (const InstDesc*)ctx->desc.p, B, Nmax, Lmax, fc, tables(ctx), fo, ctx->ws.p,
+  cudaError_t e = launch_fit(prec, y_d, (const InstDesc*)ctx->desc.p, B, Nmax, Lmax, fc, tables(ctx), fo, ctx->ws.p,
                              (int*)ctx->counter.p, grid, st);
   record(ctx, 0, st, false);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "fit kernel launch");
@@ -378,7 +379,7 @@ lse_status lse_eval_grid_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* 
                                  void* s, void* ds, void* d2s, void* stream) {
   if (!ctx || !y_d || !y_offsets || !k_offsets || !beta_d || !L || B < 1)
     return fail(ctx, LSE_EINVAL, "null argument or B < 1");
-  const bool f32 = ctx->cfg.precision == LSE_PREC_MIXED;
+  const bool f32 = ctx->cfg.precision != LSE_PREC_FP64;
   if (dtype != (f32 ? LSE_F32 : LSE_F64))
     return fail(ctx, LSE_EINVAL, "dtype must be LSE_F64 for an FP64 context and LSE_F32 for a mixed one");
   cudaSetDevice(ctx->cfg.device);
@@ -426,7 +427,7 @@ lse_status lse_eval_grid_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* 
   double* delta = (double*)(x + totN);
   int* status = (int*)(delta + B);
   record(ctx, 1, st, true);
-  cudaError_t e = launch_factor(y_d, (const InstDesc*)ctx->desc.p, B, Nmax, theta_d, gamma_d, beta_d, tables(ctx),
+  cudaError_t e = launch_factor(ctx->cfg.precision == LSE_PREC_MIXED_DF, y_d, (const InstDesc*)ctx->desc.p, B, Nmax, theta_d, gamma_d, beta_d, tables(ctx),
                                 ctx->ws.p, rho, x, delta, status, st);
   record(ctx, 1, st, false);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "factor kernel launch");
@@ -452,7 +453,7 @@ lse_status lse_eval_grid(lse_ctx* ctx, const float* y, int32_t N, const double* 
                          void* ds, void* d2s) {
   if (!ctx || !y || N < 2 || K < 0 || K > N || (K > 0 && (!theta || !gamma)) || !(beta > 0.0))
     return fail(ctx, LSE_EINVAL, "bad argument");
-  const bool f32 = ctx->cfg.precision == LSE_PREC_MIXED;
+  const bool f32 = ctx->cfg.precision != LSE_PREC_FP64;
   if (dtype != (f32 ? LSE_F32 : LSE_F64))
     return fail(ctx, LSE_EINVAL, "dtype must be LSE_F64 for an FP64 context and LSE_F32 for a mixed one");
   if (!is_pow2(L) || L < 2 * N) return fail(ctx, LSE_EINVAL, "L must be a power of two >= 2N");

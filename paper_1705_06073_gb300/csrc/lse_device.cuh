@@ -148,6 +148,7 @@ __device__ void block_first_column(c128* c, const double* theta, const double* g
 // ---------------------------------------------------------------------------
 struct LevShared {
   c128 k;        // current reflection coefficient
+  float4 kdf;    // the same as a double-float pair (double-float recursion)
   double delta;  // current pivot
   double mant;   // ln|C| accumulated as mant * 2^expo
   int expo;

@@ -29,6 +29,7 @@
 #include <cfloat>
 
 #include "lse_device.cuh"
+#include "lse_df64.cuh"
 #include "lse_internal.h"
 
 namespace lse {
@@ -142,9 +143,11 @@ __device__ __forceinline__ double mod1(double t) {
   return r;
 }
 
-template <bool MIXED>
+// PREC: 0 = FP64 throughout, 1 = FP32 grid (FP64 recursion), 2 = FP32 grid and
+// double-float recursion on the FP32 pipes.
+template <int PREC>
 struct Fitter {
-  using TG = typename std::conditional<MIXED, float, double>::type;
+  using TG = typename std::conditional<PREC != 0, float, double>::type;
   FitShared* sh;
   char* dsm;  // dynamic shared memory
   Work<TG> w;
@@ -162,7 +165,9 @@ struct Fitter {
   __device__ int evaluate(const double* th, const double* ga, int K, bool want_sums) {
     const double beta = sh->beta;
     block_first_column<kNT>(lev_c, th, ga, K, beta, N, tables);
-    LevResult lr = block_levinson<kNT>(lev_c, lev_a, N, sh->red, &sh->lev);
+    LevResult lr;
+    if constexpr (PREC == 2) lr = block_levinson_df<kNT>(lev_c, lev_a, N, (float4*)sh->red, &sh->lev);
+    else lr = block_levinson<kNT>(lev_c, lev_a, N, sh->red, &sh->lev);
     if (threadIdx.x == 0) sh->n_evals++;
     if (lr.status) {
       __syncthreads();
@@ -592,18 +597,18 @@ struct Fitter {
   }
 };
 
-template <bool MIXED>
+template <int PREC>
 __global__ void __launch_bounds__(kNT, 1) fit_kernel(FitArgs args) {
-  using TG = typename Fitter<MIXED>::TG;
+  using TG = typename Fitter<PREC>::TG;
   __shared__ FitShared sh;
   extern __shared__ __align__(16) char dsm[];
-  Fitter<MIXED> F;
+  Fitter<PREC> F;
   F.sh = &sh;
   F.dsm = dsm;
   F.A = &args;
   F.w = carve<TG>(args.ws + (size_t)blockIdx.x * args.ws_bytes, args.Nmax, args.Lmax);
   F.tw64 = Twiddles<double>{args.tab.tw64, args.tab.log2max};
-  if constexpr (MIXED) F.twg = Twiddles<TG>{(const cx<TG>*)args.tab.tw32, args.tab.log2max};
+  if constexpr (PREC != 0) F.twg = Twiddles<TG>{(const cx<TG>*)args.tab.tw32, args.tab.log2max};
   else F.twg = Twiddles<TG>{(const cx<TG>*)args.tab.tw64, args.tab.log2max};
   for (;;) {
     if (threadIdx.x == 0) sh.inst = atomicAdd(args.counter, 1);
@@ -617,13 +622,21 @@ __global__ void __launch_bounds__(kNT, 1) fit_kernel(FitArgs args) {
 
 }  // namespace
 
-size_t fit_workspace_bytes(int Nmax, int Lmax, bool mixed) {
-  return mixed ? make_layout<float>(Nmax, Lmax).total : make_layout<double>(Nmax, Lmax).total;
+size_t fit_workspace_bytes(int Nmax, int Lmax, int prec) {
+  return prec ? make_layout<float>(Nmax, Lmax).total : make_layout<double>(Nmax, Lmax).total;
 }
 int fit_smem_bytes() { return kSmemBytes; }
 int fit_threads() { return kNT; }
 
-cudaError_t launch_fit(bool mixed, const float* y, const InstDesc* inst, int B, int Nmax, int Lmax,
+template <int PREC>
+static cudaError_t launch_prec(const FitArgs& a, int grid, cudaStream_t stream) {
+  cudaError_t e = cudaFuncSetAttribute(fit_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  if (e != cudaSuccess) return e;
+  fit_kernel<PREC><<<grid, kNT, kSmemBytes, stream>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fit(int prec, const float* y, const InstDesc* inst, int B, int Nmax, int Lmax,
                        const FitConfig& cfg, const Tables& tab, const FitOut& out, void* ws, int* counter, int grid,
                        cudaStream_t stream) {
   FitArgs a;
@@ -636,19 +649,13 @@ cudaError_t launch_fit(bool mixed, const float* y, const InstDesc* inst, int B, 
   a.tab = tab;
   a.out = out;
   a.ws = (char*)ws;
-  a.ws_bytes = fit_workspace_bytes(Nmax, Lmax, mixed);
+  a.ws_bytes = fit_workspace_bytes(Nmax, Lmax, prec);
   a.counter = counter;
-  cudaError_t e;
-  if (mixed) {
-    e = cudaFuncSetAttribute(fit_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    if (e != cudaSuccess) return e;
-    fit_kernel<true><<<grid, kNT, kSmemBytes, stream>>>(a);
-  } else {
-    e = cudaFuncSetAttribute(fit_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    if (e != cudaSuccess) return e;
-    fit_kernel<false><<<grid, kNT, kSmemBytes, stream>>>(a);
+  switch (prec) {
+    case 0: return launch_prec<0>(a, grid, stream);
+    case 1: return launch_prec<1>(a, grid, stream);
+    default: return launch_prec<2>(a, grid, stream);
   }
-  return cudaGetLastError();
 }
 
 }  // namespace lse

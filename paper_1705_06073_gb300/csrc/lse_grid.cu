@@ -17,6 +17,7 @@
 //                   q = X0,  q' = -j 2 pi X1,  q'' = -4 pi^2 X2
 //                 (d = delta_{N-1}; DFT_L(v)(l) = sum_n v_n e^{-j 2 pi n l / L}).
 #include "lse_device.cuh"
+#include "lse_df64.cuh"
 #include "lse_internal.h"
 
 namespace lse {
@@ -43,6 +44,7 @@ __host__ __device__ inline FactorLayout factor_layout(int Nmax) {
   return L;
 }
 
+template <bool DF>
 __global__ void __launch_bounds__(kFNT, 1)
     factor_kernel(const float* y, const InstDesc* inst, int Nmax, const double* theta, const double* gamma,
                   const double* beta, Tables tab, char* ws, size_t ws_bytes, c128* rho_out, c128* x_out,
@@ -77,7 +79,9 @@ __global__ void __launch_bounds__(kFNT, 1)
     cc = (c128*)(base + FL.c); aa = (c128*)(base + FL.a); tables = (c128*)dsm;
   }
   block_first_column<kFNT>(cc, theta + d.k_off, gamma + d.k_off, d.K, beta[b], N, tables);
-  const LevResult lr = block_levinson<kFNT>(cc, aa, N, red, &lev);
+  LevResult lr;
+  if constexpr (DF) lr = block_levinson_df<kFNT>(cc, aa, N, (float4*)red, &lev);
+  else lr = block_levinson<kFNT>(cc, aa, N, red, &lev);
   c128* rho = rho_out + d.y_off;
   c128* x = x_out + d.y_off;
   if (lr.status) {
@@ -158,15 +162,25 @@ __global__ void __launch_bounds__(kFNT, 1)
 
 size_t factor_workspace_bytes(int Nmax) { return factor_layout(Nmax).total; }
 
-cudaError_t launch_factor(const float* y, const InstDesc* inst, int B, int Nmax, const double* theta,
+template <bool DF>
+static cudaError_t launch_factor_t(const float* y, const InstDesc* inst, int B, int Nmax, const double* theta,
+                                   const double* gamma, const double* beta, const Tables& tab, void* ws,
+                                   c128* rho_out, c128* x_out, double* delta_out, int* status, cudaStream_t stream) {
+  const int smem = 200 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(factor_kernel<DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  factor_kernel<DF><<<B, kFNT, smem, stream>>>(y, inst, Nmax, theta, gamma, beta, tab, (char*)ws,
+                                               factor_workspace_bytes(Nmax), rho_out, x_out, delta_out, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_factor(bool df, const float* y, const InstDesc* inst, int B, int Nmax, const double* theta,
                           const double* gamma, const double* beta, const Tables& tab, void* ws, c128* rho_out,
                           c128* x_out, double* delta_out, int* status, cudaStream_t stream) {
-  const int smem = 200 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  factor_kernel<<<B, kFNT, smem, stream>>>(y, inst, Nmax, theta, gamma, beta, tab, (char*)ws,
-                                           factor_workspace_bytes(Nmax), rho_out, x_out, delta_out, status);
-  return cudaGetLastError();
+  return df ? launch_factor_t<true>(y, inst, B, Nmax, theta, gamma, beta, tab, ws, rho_out, x_out, delta_out,
+                                    status, stream)
+            : launch_factor_t<false>(y, inst, B, Nmax, theta, gamma, beta, tab, ws, rho_out, x_out, delta_out,
+                                     status, stream);
 }
 
 size_t grid_workspace_bytes(int B, int64_t total_L, bool f32) {

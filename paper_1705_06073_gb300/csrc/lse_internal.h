@@ -47,19 +47,19 @@ struct Tables {
 };
 
 // Per-CTA workspace needed by the fit kernel for instances up to (Nmax, Lmax).
-size_t fit_workspace_bytes(int Nmax, int Lmax, bool mixed);
+size_t fit_workspace_bytes(int Nmax, int Lmax, int prec);
 int fit_smem_bytes();
 int fit_threads();
 
 // Launch the persistent fit kernel over B instances on `stream` with `grid`
-// CTAs; `ws` holds grid * fit_workspace_bytes(Nmax, Lmax, mixed) bytes and
+// CTAs; `ws` holds grid * fit_workspace_bytes(Nmax, Lmax, prec) bytes and
 // `counter` one zeroed int (work queue).
-cudaError_t launch_fit(bool mixed, const float* y, const InstDesc* inst, int B, int Nmax, int Lmax, const FitConfig& cfg,
+cudaError_t launch_fit(int prec, const float* y, const InstDesc* inst, int B, int Nmax, int Lmax, const FitConfig& cfg,
                        const Tables& tab, const FitOut& out, void* ws, int* counter, int grid, cudaStream_t stream);
 
 // Eval-grid: per-instance factorisation (first column, Levinson, GS apply).
 size_t factor_workspace_bytes(int Nmax);
-cudaError_t launch_factor(const float* y, const InstDesc* inst, int B, int Nmax, const double* theta,
+cudaError_t launch_factor(bool df, const float* y, const InstDesc* inst, int B, int Nmax, const double* theta,
                           const double* gamma, const double* beta, const Tables& tab, void* ws, c128* rho_out,
                           c128* x_out, double* delta_out, int* status, cudaStream_t stream);
 // Eval-grid: spectra and combine.  outputs in T (float for mixed, double for fp64).

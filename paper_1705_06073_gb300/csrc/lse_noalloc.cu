@@ -103,12 +103,12 @@ LSE_API lse_status lse_fit_noalloc_d(const lse_config* cfg, const float* y_d, in
   const int L = c.grid_size ? c.grid_size : 1 << (int)std::lround(std::log2(8.0 * N));
   if ((L & (L - 1)) || L < 2 * N || L > (1 << kMaxLog2L))
     return set_err(LSE_EINVAL, "lse_fit_noalloc_d: L must be a power of two with 2N <= L <= 32768");
-  if (c.precision != LSE_PREC_FP64 && c.precision != LSE_PREC_MIXED)
+  if (c.precision != LSE_PREC_FP64 && c.precision != LSE_PREC_MIXED && c.precision != LSE_PREC_MIXED_DF)
     return set_err(LSE_EINVAL, "lse_fit_noalloc_d: unknown precision");
   if (c.max_outer < 1 || c.max_inner < 0 || c.approx_activation_iters < 0 || !(c.tau >= 0.0))
     return set_err(LSE_EINVAL, "lse_fit_noalloc_d: bad iteration limits or tau");
-  const bool mixed = c.precision == LSE_PREC_MIXED;
-  if (fit_workspace_bytes(N, L, mixed) > kScratchBytes)
+  const int prec = c.precision;
+  if (fit_workspace_bytes(N, L, prec) > kScratchBytes)
     return set_err(LSE_EINVAL, "lse_fit_noalloc_d: workspace for this N and L exceeds the 8 MiB static scratch");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
@@ -125,7 +125,7 @@ LSE_API lse_status lse_fit_noalloc_d(const lse_config* cfg, const float* y_d, in
   const FitOut fo{out->theta, out->gamma, (c128*)out->alpha, out->K, out->beta, out->objective, out->iters,
                   out->n_evals, out->n_grid, out->status};
   const Tables tab{d->tw64, d->tw32, kMaxLog2L};
-  if (launch_fit(mixed, y_d, d->desc, 1, N, L, fc, tab, fo, d->scratch, d->counter, 1, st) != cudaSuccess)
+  if (launch_fit(prec, y_d, d->desc, 1, N, L, fc, tab, fo, d->scratch, d->counter, 1, st) != cudaSuccess)
     return set_err(LSE_ECUDA, "lse_fit_noalloc_d: fit kernel launch failed");
   return LSE_OK;
 }

@@ -34,9 +34,17 @@ def check(gpu, ref, tol_theta=1e-6, tol_rel=1e-6):
     assert abs(gpu["objective"] - ref.objective) <= tol_rel * max(1.0, abs(ref.objective))
 
 
-def test_fit_single_n256(lse_mod):
+PRECS = ["fp64", "mixed", "mixed_df"]
+
+
+def prec_of(lse, name):
+    return {"fp64": lse.LSE_PREC_FP64, "mixed": lse.LSE_PREC_MIXED, "mixed_df": lse.LSE_PREC_MIXED_DF}[name]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_fit_single_n256(lse_mod, prec):
     inst, L = synth.single_n256()[0]
-    ctx = make_ctx(lse_mod, L)
+    ctx = make_ctx(lse_mod, L, precision=prec_of(lse_mod, prec))
     try:
         gpu = lse_mod.lse_fit(ctx, inst.y)
     finally:
@@ -48,12 +56,13 @@ def test_fit_single_n256(lse_mod):
     assert gpu["n_grid"] == ref.n_grid_evals
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("N,K,snr,seed", [(64, 3, 25.0, 1), (100, 4, 15.0, 2), (128, 10, 20.0, 3), (37, 2, 30.0, 4),
-                                          (200, 6, 10.0, 5)])
-def test_fit_small_instances(lse_mod, N, K, snr, seed):
+                                          (200, 6, 10.0, 5), (1024, 16, 25.0, 6)])
+def test_fit_small_instances(lse_mod, N, K, snr, seed, prec):
     inst = synth.make_instance(N, K, snr, 7000 + seed)
     L = synth.default_grid_size(N)
-    ctx = make_ctx(lse_mod)
+    ctx = make_ctx(lse_mod, precision=prec_of(lse_mod, prec))
     try:
         gpu = lse_mod.lse_fit(ctx, inst.y)
     finally:
@@ -62,11 +71,12 @@ def test_fit_small_instances(lse_mod, N, K, snr, seed):
     check(gpu, ref)
 
 
-def test_fit_batch_ragged_matches_single_fits(lse_mod):
+@pytest.mark.parametrize("prec", PRECS)
+def test_fit_batch_ragged_matches_single_fits(lse_mod, prec):
     """One launch over instances of different N; each equals the oracle's fit."""
     specs = [(48, 2), (130, 5), (77, 3), (256, 8), (33, 1), (160, 4)]
     insts = [synth.make_instance(N, K, 20.0, 8000 + i) for i, (N, K) in enumerate(specs)]
-    ctx = make_ctx(lse_mod)
+    ctx = make_ctx(lse_mod, precision=prec_of(lse_mod, prec))
     try:
         res = lse_mod.lse_fit_batch(ctx, [i.y for i in insts])
     finally:

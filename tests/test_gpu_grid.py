@@ -24,9 +24,10 @@ def ctxs():
     build.build()
     c64 = lse.lse_create(lse.lse_config_default(precision=lse.LSE_PREC_FP64))
     cmx = lse.lse_create(lse.lse_config_default(precision=lse.LSE_PREC_MIXED))
-    yield c64, cmx
-    lse.lse_destroy(c64)
-    lse.lse_destroy(cmx)
+    cdf = lse.lse_create(lse.lse_config_default(precision=lse.LSE_PREC_MIXED_DF))
+    yield c64, cmx, cdf
+    for c in (c64, cmx, cdf):
+        lse.lse_destroy(c)
 
 
 def state(N, K, seed):
@@ -53,11 +54,12 @@ def test_grid_fp64_matches_oracle(ctxs, N, K, L):
     assert np.all(np.abs(got["s"] - ref["s"]) <= 1e-8 * ref["s"])
 
 
+@pytest.mark.parametrize("which", [1, 2])
 @pytest.mark.parametrize("N,K,L", CASES)
-def test_grid_mixed_matches_oracle(ctxs, N, K, L):
+def test_grid_mixed_matches_oracle(ctxs, N, K, L, which):
     from paper_1705_06073_gb300 import lse
     y, th, ga, be = state(N, K, 2000 + N)
-    got = lse.lse_eval_grid(ctxs[1], y, th, ga, be, L, f64=False)
+    got = lse.lse_eval_grid(ctxs[which], y, th, ga, be, L, f64=False)
     ref = dn.DenseEval(y, th, ga, be).grid(L, derivatives=True)
     err = grid_errors(got, ref, N)
     assert max(err.values()) < 1e-4, err
