@@ -54,9 +54,11 @@ typedef enum lse_status {
 /* Arithmetic of the hot path.
  * LSE_PREC_FP64: every step in FP64 (the plain path).
  * LSE_PREC_MIXED: first column, Levinson recursion, Gohberg-Semencul apply,
- *   objective, beta and gamma updates in FP64; grid FFTs, the grid
- *   combine/search and the Newton sums in FP32 (complex64); grid decisions
- *   are re-scored in FP64 before they are taken.
+ *   objective, off-grid Newton sums, beta and gamma updates in FP64; grid
+ *   FFTs and the grid combine/search in FP32 (complex64); every grid
+ *   decision (argmin, approximate-activation candidates) is re-scored in
+ *   FP64 before it is taken.  (FP32 Newton sums were measured to break the
+ *   line search, so they stay FP64.)
  * LSE_PREC_MIXED_DF: as LSE_PREC_MIXED, but the Levinson recursion runs in
  *   double-float arithmetic (pairs of FP32 numbers, 48-bit significand) on
  *   the FP32 pipes, which on GB300 are ~70x faster than its FP64 pipe. */

@@ -36,11 +36,15 @@ namespace lse {
 
 namespace {
 
-constexpr int kNT = 256;         // threads per block
+// threads per block: the double-float recursion needs more warps in flight to
+// hide its dependency chains; the FP64 paths are bound by the FP64 pipe.
+template <int PREC>
+__host__ __device__ constexpr int threads_for() { return PREC == 2 ? 512 : 256; }
 constexpr int kSmemBytes = 200 * 1024;
 constexpr double kEpsL = 2.220446049250313e-16;
 constexpr int kST_OK = 0, kST_NUMERIC = 4, kST_NOTCONV = 5;
 
+template <int kNT>
 struct FitShared {
   c128 red[kNT];
   MinLoc ml[kNT / 32];
@@ -51,22 +55,33 @@ struct FitShared {
   double beta, zeta, eps_beta, tau;
   double logdet, yCy, delta_last, f_cur, yy;
   double lpo, gbar;
+  // grid decisions of the mixed paths: best FP32 candidates re-scored in FP64
+  int ntop, sel;
+  int top[32];
+  double top_dl[32], top_s[32];
+  c128 top_q[32];
 };
 
 // Per-block global workspace for an instance of size up to (Nmax, Lmax).
 template <class TG>
 struct Work {
   c128 *y, *c, *a, *rho, *x, *Yf;
-  c128* buf[5];   // FFT buffers, M2max each (GS apply)
+  c128* buf[5];     // FFT buffers, M2max each (GS apply)
   cx<TG>* gbuf[4];  // grid FFT buffers, Lmax each
   double *theta, *gamma, *th_t, *ga_t, *dth, *dga;
-  c128* sums;     // 7 * Nmax
-  double* dl;     // Lmax
-  int* cand;      // Lmax
+  c128* sums;       // 7 * Nmax off-grid sums (FP64 on every path)
+  double* dl;       // Lmax
+  int* cand;        // Lmax
+  double *cand_dl, *cand_s;  // Lmax: decision values of the candidates
+  c128* cand_q;     // Lmax
+  double* rs_theta;  // kRescore: frequencies being re-scored
+  c128* rs_sums;     // 7 * kRescore
 };
 
+constexpr int kRescore = 1024;  // grid points re-scored in FP64 per batch
+
 struct Layout {
-  size_t off[32];
+  size_t off[40];
   size_t total;
 };
 
@@ -85,6 +100,11 @@ __host__ __device__ inline Layout make_layout(int Nmax, int Lmax) {
   put(sizeof(c128) * 7 * (size_t)Nmax);                                 // sums
   put(sizeof(double) * (size_t)Lmax);                                   // dl
   put(sizeof(int) * (size_t)Lmax);                                      // cand
+  put(sizeof(double) * (size_t)Lmax);                                   // cand_dl
+  put(sizeof(double) * (size_t)Lmax);                                   // cand_s
+  put(sizeof(c128) * (size_t)Lmax);                                     // cand_q
+  put(sizeof(double) * (size_t)kRescore);                               // rs_theta
+  put(sizeof(c128) * 7 * (size_t)kRescore);                             // rs_sums
   L.total = o;
   return L;
 }
@@ -112,6 +132,11 @@ __device__ Work<TG> carve(char* base, int Nmax, int Lmax) {
   w.sums = (c128*)(base + L.off[i++]);
   w.dl = (double*)(base + L.off[i++]);
   w.cand = (int*)(base + L.off[i++]);
+  w.cand_dl = (double*)(base + L.off[i++]);
+  w.cand_s = (double*)(base + L.off[i++]);
+  w.cand_q = (c128*)(base + L.off[i++]);
+  w.rs_theta = (double*)(base + L.off[i++]);
+  w.rs_sums = (c128*)(base + L.off[i++]);
   return w;
 }
 
@@ -147,8 +172,9 @@ __device__ __forceinline__ double mod1(double t) {
 // double-float recursion on the FP32 pipes.
 template <int PREC>
 struct Fitter {
+  static constexpr int kNT = threads_for<PREC>();
   using TG = typename std::conditional<PREC != 0, float, double>::type;
-  FitShared* sh;
+  FitShared<kNT>* sh;
   char* dsm;  // dynamic shared memory
   Work<TG> w;
   const FitArgs* A;
@@ -187,12 +213,15 @@ struct Fitter {
       sh->f_cur = lr.logdet + yCy;
     }
     __syncthreads();
-    if (want_sums && K > 0) block_active_sums<kNT, double>(w.rho, w.x, th, K, N, w.sums);
+    if (want_sums && K > 0) compute_sums(th, K);
     return 0;
   }
 
-  __device__ void compute_sums(int K) {
-    if (K > 0) block_active_sums<kNT, double>(w.rho, w.x, w.theta, K, N, w.sums);
+  // The Newton sums stay FP64 on every path: in FP32 the gradient terms
+  // (e.g. s - |q|^2 near convergence) cancel catastrophically, the Newton
+  // directions disagree with the FP64 objective and the line search stalls.
+  __device__ void compute_sums(const double* th, int K) {
+    if (K > 0) block_active_sums<kNT, double>(w.rho, w.x, th, K, N, w.sums);
   }
 
   // ---------------------------------------------------------------- grid ---
@@ -239,6 +268,61 @@ struct Fitter {
     s = 2.0 / sh->delta_last * (Q1 * conj(Q0)).re;
   }
 
+  // Delta L of eq. (delta_L) from s and q at a grid point.
+  __device__ double delta_L(double s, c128 q, int K) const {
+    const double aq2 = norm2(q);
+    double gb = sh->gbar;
+    if (K == 0) gb = aq2 > s ? (aq2 - s) / (s * s) : 0.0;
+    return log1p(gb * s) + sh->lpo - gb * aq2 / (1.0 + gb * s);
+  }
+
+  // FP64 re-evaluation of s, q and Delta L at grid points ls[0..n), n <=
+  // kRescore, by the direct off-grid sums of Sec. IV-B/C on the FP64
+  // generators (mixed paths: the FP32 grid only proposes candidates).
+  __device__ void rescore(const int* ls, int n, double* dl_out, double* s_out, c128* q_out, int K) {
+    for (int j = threadIdx.x; j < n; j += kNT) w.rs_theta[j] = (double)ls[j] / (double)L;
+    __syncthreads();
+    block_active_sums<kNT, double>(w.rho, w.x, w.rs_theta, n, N, w.rs_sums);
+    const double inv_delta = 1.0 / sh->delta_last;
+    for (int j = threadIdx.x; j < n; j += kNT) {
+      const c128* sm = w.rs_sums + 7 * j;
+      const double sv = 2.0 * inv_delta * (sm[1] * conj(sm[0])).re;
+      const c128 qv = sm[4];
+      dl_out[j] = delta_L(sv, qv, K);
+      s_out[j] = sv;
+      q_out[j] = qv;
+    }
+    __syncthreads();
+  }
+
+  // The 8 smallest grid values of Delta L and their cyclic neighbours into
+  // sh->top (deduplicated), then re-scored in FP64 into sh->top_dl/s/q.
+  __device__ void top_candidates(int K) {
+    if (threadIdx.x == 0) sh->ntop = 0;
+    __syncthreads();
+    for (int r = 0; r < 8; ++r) {
+      const int nt = sh->ntop;
+      MinLoc m{HUGE_VAL, 0x7fffffff};
+      for (int l = threadIdx.x; l < L; l += kNT) {
+        bool taken = false;
+        for (int j = 0; j < nt; ++j) taken |= (sh->top[j] == l);
+        if (!taken) m = minloc(m, MinLoc{w.dl[l], l});
+      }
+      m = block_minloc<kNT>(m, sh->ml);
+      if (m.i == 0x7fffffff) break;
+      if (threadIdx.x == 0) {
+        for (int dd = -1; dd <= 1; ++dd) {
+          const int l2 = (m.i + dd + L) & (L - 1);
+          bool have = false;
+          for (int j = 0; j < sh->ntop; ++j) have |= (sh->top[j] == l2);
+          if (!have && sh->ntop < 32) sh->top[sh->ntop++] = l2;
+        }
+      }
+      __syncthreads();
+    }
+    rescore(sh->top, sh->ntop, sh->top_dl, sh->top_s, sh->top_q, K);
+  }
+
   // ---------------------------------------------------- exact activation ---
   __device__ int exact_activation(bool have_grid) {
     int n_act = 0;
@@ -247,12 +331,25 @@ struct Fitter {
       if (!have_grid) grid_delta(K);
       have_grid = false;
       MinLoc m{HUGE_VAL, 0x7fffffff};
-      for (int l = threadIdx.x; l < L; l += kNT) m = minloc(m, MinLoc{w.dl[l], l});
-      m = block_minloc<kNT>(m, sh->ml);
+      if constexpr (PREC == 0) {
+        for (int l = threadIdx.x; l < L; l += kNT) m = minloc(m, MinLoc{w.dl[l], l});
+        m = block_minloc<kNT>(m, sh->ml);
+      } else {
+        top_candidates(K);
+        for (int j = 0; j < sh->ntop; ++j) m = minloc(m, MinLoc{sh->top_dl[j], sh->top[j]});
+      }
       if (threadIdx.x == 0) {
         double s;
         c128 q;
-        grid_point(m.i, s, q);
+        if constexpr (PREC == 0) {
+          grid_point(m.i, s, q);
+        } else {
+          int jm = 0;
+          for (int j = 0; j < sh->ntop; ++j)
+            if (sh->top[j] == m.i) jm = j;
+          s = sh->top_s[jm];
+          q = sh->top_q[jm];
+        }
         const double aq2 = norm2(q);
         const double ghat = aq2 > s ? (aq2 - s) / (s * s) : 0.0;
         const double gb = K ? sh->gbar : ghat;
@@ -286,18 +383,26 @@ struct Fitter {
     grid_delta(K0);
     grid_valid = true;  // until a component is activated the grid stays that of the current state
     // global minimum of Delta L (equals the minimum over the local minima)
-    MinLoc m{HUGE_VAL, 0x7fffffff};
-    for (int l = threadIdx.x; l < L; l += kNT) m = minloc(m, MinLoc{w.dl[l], l});
-    m = block_minloc<kNT>(m, sh->ml);
-    const double dlmin = m.v;
+    double dlmin, slack = 0.0;
+    if constexpr (PREC == 0) {
+      MinLoc m{HUGE_VAL, 0x7fffffff};
+      for (int l = threadIdx.x; l < L; l += kNT) m = minloc(m, MinLoc{w.dl[l], l});
+      m = block_minloc<kNT>(m, sh->ml);
+      dlmin = m.v;
+    } else {
+      top_candidates(K0);
+      dlmin = HUGE_VAL;
+      for (int j = 0; j < sh->ntop; ++j) dlmin = fmin(dlmin, sh->top_dl[j]);
+    }
     if (!(dlmin < 0.0)) return 0;
     const double thr = dlmin / 5.0;
+    if constexpr (PREC != 0) slack = 1e-3 * fabs(thr);  // FP32 grid error, candidates re-scored below
     if (threadIdx.x == 0) sh->cand_count = 0;
     __syncthreads();
     for (int l = threadIdx.x; l < L; l += kNT) {
       const double v = w.dl[l];
       const double vl = w.dl[(l + L - 1) & (L - 1)], vr = w.dl[(l + 1) & (L - 1)];
-      if (v < vl && v <= vr && v <= thr) {
+      if (v < vl && v <= vr && v <= thr + slack) {
         const int slot = atomicAdd(&sh->cand_count, 1);
         w.cand[slot] = l;
       }
@@ -305,20 +410,40 @@ struct Fitter {
     __syncthreads();
     const int nc = sh->cand_count;
     __syncthreads();
+    // decision values of every candidate: the FP64 grid (FP64 path) or an FP64
+    // re-evaluation (mixed paths)
+    if constexpr (PREC == 0) {
+      for (int j = threadIdx.x; j < nc; j += kNT) {
+        const int l = w.cand[j];
+        double sv;
+        c128 qv;
+        grid_point(l, sv, qv);
+        w.cand_dl[j] = w.dl[l];
+        w.cand_s[j] = sv;
+        w.cand_q[j] = qv;
+      }
+      __syncthreads();
+    } else {
+      for (int j0 = 0; j0 < nc; j0 += kRescore)
+        rescore(w.cand + j0, min(kRescore, nc - j0), w.cand_dl + j0, w.cand_s + j0, w.cand_q + j0, K0);
+    }
     int n_act = 0;
     const double min_sep = 0.05 / (double)N;
     for (int it = 0; it < nc; ++it) {
       MinLoc b{HUGE_VAL, 0x7fffffff};
       for (int j = threadIdx.x; j < nc; j += kNT) {
         const int l = w.cand[j];
-        if (l >= 0) b = minloc(b, MinLoc{w.dl[l], l});
+        if (l >= 0 && w.cand_dl[j] <= thr) b = minloc(b, MinLoc{w.cand_dl[j], l});
       }
       b = block_minloc<kNT>(b, sh->ml);
       if (b.i == 0x7fffffff) break;
       const int l = b.i;
-      // strike it out
+      // strike it out and remember its slot
       for (int j = threadIdx.x; j < nc; j += kNT)
-        if (w.cand[j] == l) w.cand[j] = -1;
+        if (w.cand[j] == l) {
+          w.cand[j] = -1;
+          sh->sel = j;
+        }
       const double th = (double)l / (double)L;
       int close = 0;
       for (int k = threadIdx.x; k < sh->K; k += kNT) {
@@ -328,9 +453,8 @@ struct Fitter {
       }
       close = __syncthreads_or(close);
       if (threadIdx.x == 0 && !close && sh->K < N) {
-        double s;
-        c128 q;
-        grid_point(l, s, q);
+        const double s = w.cand_s[sh->sel];
+        const c128 q = w.cand_q[sh->sel];
         const double aq2 = norm2(q);
         const double ghat = aq2 > s ? (aq2 - s) / (s * s) : 0.0;
         const double gb = K0 ? sh->gbar : ghat;
@@ -395,7 +519,7 @@ struct Fitter {
           w.gamma[k] = w.ga_t[k];
         }
         __syncthreads();
-        compute_sums(K);
+        compute_sums(w.theta, K);
         return dec;
       }
       alpha *= 0.5;
@@ -598,9 +722,9 @@ struct Fitter {
 };
 
 template <int PREC>
-__global__ void __launch_bounds__(kNT, 1) fit_kernel(FitArgs args) {
+__global__ void __launch_bounds__(threads_for<PREC>(), 1) fit_kernel(FitArgs args) {
   using TG = typename Fitter<PREC>::TG;
-  __shared__ FitShared sh;
+  __shared__ FitShared<threads_for<PREC>()> sh;
   extern __shared__ __align__(16) char dsm[];
   Fitter<PREC> F;
   F.sh = &sh;
@@ -626,13 +750,12 @@ size_t fit_workspace_bytes(int Nmax, int Lmax, int prec) {
   return prec ? make_layout<float>(Nmax, Lmax).total : make_layout<double>(Nmax, Lmax).total;
 }
 int fit_smem_bytes() { return kSmemBytes; }
-int fit_threads() { return kNT; }
 
 template <int PREC>
 static cudaError_t launch_prec(const FitArgs& a, int grid, cudaStream_t stream) {
   cudaError_t e = cudaFuncSetAttribute(fit_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   if (e != cudaSuccess) return e;
-  fit_kernel<PREC><<<grid, kNT, kSmemBytes, stream>>>(a);
+  fit_kernel<PREC><<<grid, threads_for<PREC>(), kSmemBytes, stream>>>(a);
   return cudaGetLastError();
 }
 

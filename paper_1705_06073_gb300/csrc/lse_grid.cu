@@ -25,6 +25,8 @@ namespace lse {
 namespace {
 
 constexpr int kFNT = 256;
+template <bool DF>
+__host__ __device__ constexpr int factor_threads() { return DF ? 512 : 256; }
 
 struct FactorLayout {
   size_t y, c, a, Yf, buf, total, M2;
@@ -45,12 +47,12 @@ __host__ __device__ inline FactorLayout factor_layout(int Nmax) {
 }
 
 template <bool DF>
-__global__ void __launch_bounds__(kFNT, 1)
+__global__ void __launch_bounds__(factor_threads<DF>(), 1)
     factor_kernel(const float* y, const InstDesc* inst, int Nmax, const double* theta, const double* gamma,
                   const double* beta, Tables tab, char* ws, size_t ws_bytes, c128* rho_out, c128* x_out,
                   double* delta_out, int* status) {
+  constexpr int kFNT = factor_threads<DF>();
   __shared__ c128 red[kFNT];
-  __shared__ double dred[kFNT / 32];
   __shared__ LevShared lev;
   extern __shared__ __align__(16) char dsm[];
   const int b = blockIdx.x;
@@ -93,7 +95,6 @@ __global__ void __launch_bounds__(kFNT, 1)
   block_fft<kFNT, double>([=] __device__(int i) { return i < N ? yv[i] : zero<double>(); }, Yf, bufs[4], log2M2, false,
                           tw);
   block_gs_apply<kFNT>(rho, Yf, x, N, log2M2, lr.delta_last, bufs, tw);
-  (void)dred;
   if (threadIdx.x == 0) { status[b] = 0; delta_out[b] = lr.delta_last; }
 }
 
@@ -169,7 +170,7 @@ static cudaError_t launch_factor_t(const float* y, const InstDesc* inst, int B, 
   const int smem = 200 * 1024;
   cudaError_t e = cudaFuncSetAttribute(factor_kernel<DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  factor_kernel<DF><<<B, kFNT, smem, stream>>>(y, inst, Nmax, theta, gamma, beta, tab, (char*)ws,
+  factor_kernel<DF><<<B, factor_threads<DF>(), smem, stream>>>(y, inst, Nmax, theta, gamma, beta, tab, (char*)ws,
                                                factor_workspace_bytes(Nmax), rho_out, x_out, delta_out, status);
   return cudaGetLastError();
 }

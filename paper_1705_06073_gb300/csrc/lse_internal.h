@@ -49,7 +49,6 @@ struct Tables {
 // Per-CTA workspace needed by the fit kernel for instances up to (Nmax, Lmax).
 size_t fit_workspace_bytes(int Nmax, int Lmax, int prec);
 int fit_smem_bytes();
-int fit_threads();
 
 // Launch the persistent fit kernel over B instances on `stream` with `grid`
 // CTAs; `ws` holds grid * fit_workspace_bytes(Nmax, Lmax, prec) bytes and
