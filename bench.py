@@ -1,8 +1,8 @@
 #!/usr/bin/env python3
 """Throughput of the superfast line-spectral-estimation hot path on GB300.
 
-One step = one complete fit (every step of Sec. III-D/III-E with the
-superfast evaluations of Sec. IV) of a batch of 64 synthetic instances with
+One step = one complete fit (every step of Sec. II-D/II-E with the
+superfast evaluations of Sec. III) of a batch of 64 synthetic instances with
 N = 4096 complex64 samples, K = 64 sinusoids (separation 2/N, alpha ~
 CN(0,1)), SNR uniform on [10, 30] dB per instance and an L = 4N = 16384
 point grid, in one launch of the persistent fit kernel.  The headline path
@@ -53,7 +53,7 @@ def levinson_df_flops(n: int) -> float:
 
 
 def grid_bytes(n: int, l: int, f64: bool) -> float:
-    """Algorithmic bytes of one grid evaluation (Sec. IV-D): read rho and x
+    """Algorithmic bytes of one grid evaluation (Sec. III-D): read rho and x
     (n complex128 each) and write q, q', q'' (complex) and s, s', s'' (real)
     at l points."""
     es = 8 if f64 else 4

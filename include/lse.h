@@ -3,10 +3,10 @@
  *
  * The method is the block-coordinate-descent estimator of Hansen, Fleury and
  * Rao, "Superfast Line Spectral Estimation" (IEEE TSP 2018), complete-data
- * case (Sec. IV, Phi = I, M = N): given y in C^N it estimates the model order
+ * case (Sec. III, Phi = I, M = N): given y in C^N it estimates the model order
  * K and, per component, the frequency theta_k in [0,1), the coefficient
  * alpha_k and the variance gamma_k, plus the noise variance beta
- * (Sec. III, eqs. model, estModel, obj).
+ * (Sec. II, eqs. model, estModel, obj).
  *
  * Conventions shared by every entry point
  * ----------------------------------------
@@ -72,12 +72,12 @@ typedef struct lse_config {
   int32_t precision;               /* LSE_PREC_FP64 or LSE_PREC_MIXED */
   uint64_t hbm_budget_bytes;       /* cap on the context's device workspace; 0 = no cap */
   int32_t grid_size;               /* L for lse_fit*: 0 = 8N rounded to the nearest power of two
-                                      (Sec. III-C5 footnote); > 0: that L (a power of two >= 2N) */
+                                      (Sec. II-C5 footnote); > 0: that L (a power of two >= 2N) */
   double tau;                      /* threshold adjustment of eq. (activate_criterion); paper: 5 */
   int32_t max_outer;               /* outer-iteration cap (paper silent); default 200 */
-  int32_t max_inner;               /* (theta,gamma) updates per outer iteration (Sec. III-D): 5 */
+  int32_t max_inner;               /* (theta,gamma) updates per outer iteration (Sec. II-D): 5 */
   int32_t approx_activation_iters; /* outer iterations that may use the approximate activation
-                                      of Sec. III-E; default 10; 0 disables it */
+                                      of Sec. II-E; default 10; 0 disables it */
   uint64_t flags;                  /* reserved, must be 0 */
 } lse_config;
 
@@ -98,13 +98,13 @@ typedef struct lse_result {
   double objective;   /* out: eq. (obj) at the returned state, without the constant */
   int32_t iters;      /* out: outer iterations run */
   int32_t n_evals;    /* out: model evaluations (factorisations of C) */
-  int32_t n_grid;     /* out: grid evaluations (activation searches, Sec. III-C5) */
+  int32_t n_grid;     /* out: grid evaluations (activation searches, Sec. II-C5) */
 } lse_result;
 
 /* Device-resident results of a batched fit.  Instance b owns the slice
  * [off_b, off_b + N_b) of theta, gamma and alpha (complex, interleaved) where
  * off_b is the instance's offset in the y batch: K <= N always (K_max = N,
- * footnote in Sec. III-A), so the slice always fits.  All arrays are device
+ * footnote in Sec. II-A), so the slice always fits.  All arrays are device
  * memory owned by the caller. */
 typedef struct lse_batch_out {
   double* theta;      /* [sum N_b] */
@@ -132,7 +132,7 @@ LSE_API const char* lse_strerror(lse_status s);
 /* Detail of the last failing call on this context (empty if none). */
 LSE_API const char* lse_last_error(const lse_ctx* ctx);
 
-/* Fit one instance (Sec. III algorithm; superfast evaluations of Sec. IV).
+/* Fit one instance (Sec. II algorithm; superfast evaluations of Sec. III).
  * y: host, complex64 [2*N floats]; 2 <= N <= 131072.  On LSE_ECAPACITY out->K holds
  * the number of components and the arrays are not written.  Blocks until the
  * result is in out. */
@@ -154,12 +154,12 @@ LSE_API lse_status lse_fit_batch(lse_ctx* ctx, const float* y, const int64_t* of
 LSE_API lse_status lse_fit_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* offsets, int32_t B,
                            const lse_batch_out* out, void* stream);
 
-/* Grid evaluation (Sec. IV-D): for C = beta I + sum_k gamma_k psi(theta_k)
+/* Grid evaluation (Sec. III-D): for C = beta I + sum_k gamma_k psi(theta_k)
  * psi(theta_k)^H (eq. py), compute on theta_l = l/L, l = 0..L-1,
  *   q(theta) = psi(theta)^H C^{-1} y,   s(theta) = psi(theta)^H C^{-1} psi(theta)
  * and their first and second theta-derivatives.  All components given are
  * active; the evaluation uses the full C (C_{~k} = C for a component that is
- * not in the set, Sec. IV-D).  Host pointers; y complex64 [2N]; theta, gamma
+ * not in the set, Sec. III-D).  Host pointers; y complex64 [2N]; theta, gamma
  * [K] (K >= 0); beta > 0; L a power of two with L >= 2N.  Outputs: q, dq, d2q
  * complex [2L], s, ds, d2s real [L], element type dtype (LSE_F64 for an
  * LSE_PREC_FP64 context, LSE_F32 for LSE_PREC_MIXED); any output may be NULL.

@@ -12,10 +12,10 @@ It shares no code with the CUDA path.  Only ``tests/``,
 Modules
 -------
 dense   one evaluation of the model at a state (theta, gamma, beta): C, ln|C|,
-        C^{-1}y, the vectors q..x of Sec. III-C, the derivatives, the grid
+        C^{-1}y, the vectors q..x of Sec. II-C, the derivatives, the grid
         quantities and the Gohberg-Semencul generators read off the dense
         inverse.
-fit     the block-coordinate-descent estimator of Sec. III (outline in
-        Sec. III-D, approximate activation in Sec. III-E), with the
+fit     the block-coordinate-descent estimator of Sec. II (outline in
+        Sec. II-D, approximate activation in Sec. II-E), with the
         readings of the paper listed in its docstring.
 """

@@ -3,7 +3,7 @@
 Every function cites the passage of Hansen, Fleury & Rao, "Superfast Line
 Spectral Estimation" (IEEE TSP 2018) it follows.  Indices n run over
 0..N-1, so [psi(theta)]_n = exp(j 2 pi n theta), the paper's (n-1) for
-n = 1..N (Sec. III, eq. model).
+n = 1..N (Sec. II, eq. model).
 
 Parity status: every function here is pinned by a test in
 ``tests/test_oracle_pins.py`` against something other than itself (closed
@@ -35,12 +35,12 @@ def unit_phase(n, theta):
 
 
 def steering(N: int, theta) -> np.ndarray:
-    """Psi(theta) = [psi(theta_1) ... psi(theta_K)], N x K (Sec. III, eq. model)."""
+    """Psi(theta) = [psi(theta_1) ... psi(theta_K)], N x K (Sec. II, eq. model)."""
     return unit_phase(np.arange(N), np.atleast_1d(theta))
 
 
 def index_weights(N: int) -> np.ndarray:
-    """Diagonal of D = diag(0, 2pi, ..., 2pi(N-1)) (Sec. III-C, after eq. x)."""
+    """Diagonal of D = diag(0, 2pi, ..., 2pi(N-1)) (Sec. II-C, after eq. x)."""
     return TWO_PI * np.arange(N, dtype=np.float64)
 
 
@@ -54,7 +54,7 @@ def covariance(N: int, theta, gamma, beta: float) -> np.ndarray:
 def first_column(N: int, theta, gamma, beta: float) -> np.ndarray:
     """c_m = [C]_{m,0} = beta delta_{m0} + sum_k gamma_k e^{j 2 pi m theta_k}.
 
-    C is Hermitian Toeplitz in the complete-data case (Sec. IV intro); this is
+    C is Hermitian Toeplitz in the complete-data case (Sec. III intro); this is
     the column that defines it.
     """
     A = steering(N, theta)
@@ -101,7 +101,7 @@ class DenseEval:
         K = self.theta.shape[0]
         return self.data_term() - prior_term(K, self.N, zeta)
 
-    # ---- the vectors of Sec. III-C, eqs. (q)-(x) -----------------------------
+    # ---- the vectors of Sec. II-C, eqs. (q)-(x) -----------------------------
     def active_vectors(self):
         """q, r, s, t, u, v, x at the active frequencies (eqs. q-x, Phi = I)."""
         A = self.A
@@ -118,12 +118,12 @@ class DenseEval:
         xx = np.sum(AH * d * DW, axis=0)
         return dict(q=q, r=r, s=s.real, t=t, u=u, v=v, x=xx.real)
 
-    # ---- grid quantities (Sec. IV-D), taken straight from the definitions ---
+    # ---- grid quantities (Sec. III-D), taken straight from the definitions ---
     def grid(self, L: int, derivatives: bool = False, chunk: int = 4096, points=None):
         """q(theta), s(theta) on theta_l = l/L (or at ``points``), and optionally
         their first and second theta-derivatives.
 
-        q(theta) = psi^H C^{-1} y and s(theta) = psi^H C^{-1} psi (Sec. IV-D);
+        q(theta) = psi^H C^{-1} y and s(theta) = psi^H C^{-1} psi (Sec. III-D);
         with psi' = jD psi and psi'' = -D^2 psi the product rule gives
         q' = psi'^H C^{-1} y, q'' = psi''^H C^{-1} y,
         s' = 2 Re(psi^H C^{-1} psi'), s'' = 2 Re(psi^H C^{-1} psi'') + 2 psi'^H C^{-1} psi'.
@@ -153,7 +153,7 @@ class DenseEval:
     def gs_generators(self):
         """rho and delta_0..delta_{N-1} of eq. (gohberg-semencul).
 
-        delta_i are the pivots of C = L B L^H (Sec. IV-A): with C = G G^H,
+        delta_i are the pivots of C = L B L^H (Sec. III-A): with C = G G^H,
         delta_i = |G_ii|^2.  rho is the last column of C^{-1} scaled so that
         rho_{N-1} = 1, and delta_{N-1} = 1 / [C^{-1}]_{N-1,N-1}.
         """
@@ -189,10 +189,10 @@ def derivatives(vec, gamma, N: int):
     return g_theta, g_gamma, h_theta, h_gamma
 
 
-# ---- single-component quantities (Sec. III-C4, III-C5) ------------------------
+# ---- single-component quantities (Sec. II-C4, II-C5) ------------------------
 
 def leave_one_out(q, s, gamma):
-    """q_{~k}, s_{~k} from q_k, s_k by Woodbury (Sec. III-C4, after eq. deactivate)."""
+    """q_{~k}, s_{~k} from q_k, s_k by Woodbury (Sec. II-C4, after eq. deactivate)."""
     den = 1.0 - np.asarray(gamma) * np.asarray(s)
     return np.asarray(q) / den, np.asarray(s) / den
 
@@ -245,7 +245,7 @@ def zeta_update(K: int, N: int) -> float:
 
 
 def beta_update(ev: DenseEval, s, eps_beta: float) -> float:
-    """Eq. (betaUpdate) with the Woodbury forms of Sec. III-C3:
+    """Eq. (betaUpdate) with the Woodbury forms of Sec. II-C3:
     tr(Sigma A^H A) = sum_k beta s_k gamma_k, and ||y - A mu||^2 written as
     beta^2 ||C^{-1} y||^2 (y - A Gamma A^H C^{-1} y = beta C^{-1} y)."""
     b = ev.beta

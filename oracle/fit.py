@@ -1,8 +1,8 @@
 """The superfast-LSE estimator run with dense linear algebra (oracle; test
 infrastructure only).
 
-Block-coordinate descent on eq. (obj) in the order of Sec. III-D:
-(1) activation (Sec. III-C5; approximate multi-activation of Sec. III-E in the
+Block-coordinate descent on eq. (obj) in the order of Sec. II-D:
+(1) activation (Sec. II-C5; approximate multi-activation of Sec. II-E in the
 first iterations), (2) zeta (eq. zetaUpdate), (3) beta (eq. betaUpdate),
 (4) repeat { one (theta, gamma) update; deactivation (eq. deactivate) }.
 
@@ -12,7 +12,7 @@ design notes):
 R1  (theta, gamma) update.  One iteration of step 4a is a per-component
     diagonal Newton step: d = -g / h, with g and h from eqs. (derivative),
     (derivative2); a non-positive h is replaced by (50N)^2 for theta and
-    gamma_k^-2 for gamma (Sec. III-C1).  The step length starts at 1, is cut
+    gamma_k^-2 for gamma (Sec. II-C1).  The step length starts at 1, is cut
     to 0.99 of the distance at which the first gamma_k would reach zero, and
     is halved (at most 30 times) until the Armijo condition
     f(new) <= f + 1e-4 alpha g.d holds for f = ln|C| + y^H C^{-1} y.  If no
@@ -28,7 +28,7 @@ R4  gamma-bar (eq. delta_L) is the mean of the active gamma; with no active
 R5  Exact activation (step 1): argmin of Delta L over the grid (lowest index on
     ties); activate if gamma > 0 and eq. (activate_criterion) holds with
     tau = 5; repeat until nothing is activated.
-R6  Approximate activation (Sec. III-E) runs in outer iterations 1..10 while it
+R6  Approximate activation (Sec. II-E) runs in outer iterations 1..10 while it
     activates something; once a pass activates nothing, that iteration and all
     later ones use exact activation.  Candidates are grid points with
     Delta L(l) < Delta L(l-1) and Delta L(l) <= Delta L(l+1) (cyclic); they are
@@ -112,7 +112,7 @@ class _State:
             self.trace.append((name, self.objective()))
 
     def grid_delta(self):
-        """Grid q, s and Delta L with gamma-bar per R4 (Sec. III-C5)."""
+        """Grid q, s and Delta L with gamma-bar per R4 (Sec. II-C5)."""
         self.n_grid += 1
         g = self.ev.grid(self.L)
         q, s = g["q"], g["s"]
@@ -126,7 +126,7 @@ class _State:
 
 
 def _exact_activation(st: _State, first=None):
-    """R5: single activations until none qualifies (Sec. III-C5, step 1)."""
+    """R5: single activations until none qualifies (Sec. II-C5, step 1)."""
     n = 0
     while st.K < st.N and st.zeta > 0.0:
         q, s, gbar, dl = first if first is not None else st.grid_delta()
@@ -143,7 +143,7 @@ def _exact_activation(st: _State, first=None):
 
 
 def _approximate_activation(st: _State):
-    """R6: one pass of the approximate multi-activation scheme (Sec. III-E).
+    """R6: one pass of the approximate multi-activation scheme (Sec. II-E).
     Returns (number activated, grid data for reuse when nothing changed)."""
     if st.zeta <= 0.0 or st.K >= st.N:
         return 0, None
@@ -235,7 +235,7 @@ def _deactivation(st: _State):
 
 def fit(y, L: int, tau: float = 5.0, max_outer: int = 200, max_inner: int = 5,
         approx_iters: int = 10, trace: bool = False) -> FitResult:
-    """Run the estimator of Sec. III on y (complete data, K_max = N)."""
+    """Run the estimator of Sec. II on y (complete data, K_max = N)."""
     y = np.asarray(y, dtype=np.complex128)
     N = y.shape[0]
     tr = [] if trace else None

@@ -115,7 +115,7 @@ lse_status ensure_tables(lse_ctx* c, int log2m) {
 Tables tables(const lse_ctx* c) { return Tables{c->tw64, c->tw32, c->log2max}; }
 
 int default_L(int N) {
-  // 8N rounded to the nearest power of two (Sec. III-C5 footnote)
+  // 8N rounded to the nearest power of two (Sec. II-C5 footnote)
   double l = std::log2(8.0 * N);
   return 1 << (int)std::lround(l);
 }

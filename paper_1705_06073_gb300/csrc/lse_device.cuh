@@ -1,5 +1,5 @@
 // lse_device.cuh -- block-level building blocks of the superfast evaluation
-// (Sec. IV of Hansen, Fleury, Rao, "Superfast Line Spectral Estimation").
+// (Sec. III of Hansen, Fleury, Rao, "Superfast Line Spectral Estimation").
 //
 // Every function here is executed by one whole thread block (NT threads) on
 // data of one problem instance; arrays are generic pointers (shared or
@@ -85,7 +85,7 @@ __device__ void block_fft(Gen gen, cx<T>* dst, cx<T>* tmp, int log2M, bool inver
 }
 
 // ---------------------------------------------------------------------------
-// First column of C (Sec. IV intro; C of eq. py):
+// First column of C (Sec. III intro; C of eq. py):
 //   c_m = beta [m = 0] + sum_k gamma_k exp(j 2 pi m theta_k),  m = 0..N-1.
 // m is split as m = S h + l (S = 2^ceil(log2 sqrt N)); per component the
 // shared tables gamma_k e^{j2pi l theta_k} and e^{j2pi S h theta_k} (exact
@@ -134,13 +134,13 @@ __device__ void block_first_column(c128* c, const double* theta, const double* g
 // ---------------------------------------------------------------------------
 // Levinson-Durbin recursion for the Hermitian positive definite Toeplitz C
 // with first column c (the O(N^2) route to the Gohberg-Semencul generators,
-// Sec. IV intro).  Order n -> n+1:
+// Sec. III intro).  Order n -> n+1:
 //   e_n = sum_{i<n} a_i c_{n-i},  k = -e_n / delta_{n-1},
 //   a_i <- a_i + k conj(a_{n-i})  (i = 0..n, a_n = 0 before),
 //   delta_n = delta_{n-1} (1 - |k|^2).
 // a solves C a = delta_{N-1} e_0, so the last column of C^{-1} normalised to
 // end in 1 (eq. gohberg-semencul) is rho_n = conj(a_{N-1-n}); delta_n are the
-// pivots of C = L B L^H and ln|C| = sum_n ln delta_n (Sec. IV-A).
+// pivots of C = L B L^H and ln|C| = sum_n ln delta_n (Sec. III-A).
 // The update and the next inner product are fused: the thread owning the pair
 // (i, n-i) updates both entries and adds their terms of e_{n+1}, so every
 // order costs one pass over a and two barriers.
@@ -225,7 +225,7 @@ __device__ LevResult block_levinson(const c128* c, c128* a, int N, c128* red, Le
 }
 
 // ---------------------------------------------------------------------------
-// x = C^{-1} y by eq. (gohberg-semencul) (Sec. IV-A, IV-B):
+// x = C^{-1} y by eq. (gohberg-semencul) (Sec. III-A, III-B):
 //   x = delta_{N-1}^{-1} (T1^H (T1 y) - T0 (T0^H y)),
 // [T0]_{ik} = rho_{i-k-1}, [T1]_{ik} = rho_{N-1+i-k}.  Each triangular
 // Toeplitz product is a linear convolution done with length-M2 FFTs
@@ -264,7 +264,7 @@ __device__ void block_gs_apply(const c128* rho, const c128* Yf, c128* x, int N, 
 }
 
 // ---------------------------------------------------------------------------
-// Off-grid sums at the active frequencies (Sec. IV-B, IV-C).  With the
+// Off-grid sums at the active frequencies (Sec. III-B, III-C).  With the
 // centre c = (N-2)/2 and phases e^{-j 2 pi n theta_k}:
 //   R_a = sum_n (n-c)^a rho_n e^{-j2pi n theta},  a = 0..3
 //   X_a = sum_n (n-c)^a x_n  e^{-j2pi n theta},  a = 0..2   (x = C^{-1} y).

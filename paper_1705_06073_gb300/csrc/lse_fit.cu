@@ -1,15 +1,15 @@
 // lse_fit.cu -- persistent fit kernel: one thread block runs the whole
-// block-coordinate-descent estimator (Sec. III-D, III-E of Hansen, Fleury,
+// block-coordinate-descent estimator (Sec. II-D, II-E of Hansen, Fleury,
 // Rao, "Superfast Line Spectral Estimation") for one instance at a time,
 // pulling instances from a device work counter, with every model evaluation
-// done by the superfast route of Sec. IV (Levinson recursion for the
+// done by the superfast route of Sec. III (Levinson recursion for the
 // Gohberg-Semencul generators, FFT convolutions, FFT grid, direct off-grid
 // sums).
 //
 // Readings of the paper (the same ones the CPU oracle follows):
 //  - (theta, gamma) update: one per-component diagonal Newton step with the
 //    diagonal Hessian of eqs. (derivative2) (non-positive entries replaced by
-//    (50N)^2 and gamma^-2, Sec. III-C1), step cut to 0.99 of the distance at
+//    (50N)^2 and gamma^-2, Sec. II-C1), step cut to 0.99 of the distance at
 //    which a gamma would reach 0, Armijo backtracking (c = 1e-4, <= 30
 //    halvings) on ln|C| + y^H C^{-1} y; theta modulo 1.
 //  - step 4 runs <= max_inner iterations and stops after the iteration whose
@@ -225,7 +225,7 @@ struct Fitter {
   }
 
   // ---------------------------------------------------------------- grid ---
-  // q(theta_l), s(theta_l) on the L-point grid (Sec. IV-D) from length-L FFTs:
+  // q(theta_l), s(theta_l) on the L-point grid (Sec. III-D) from length-L FFTs:
   //   Q0 = FFT(rho), Q1 = FFT((n-c) rho_n), q = FFT(x), s = 2 Re(Q1 conj Q0)/delta
   // and Delta L(theta_l) of eq. (delta_L) with gamma-bar = gbar (K > 0) or the
   // point's own eq. (activate_gamma) value (K = 0).  Fills w.dl.
@@ -277,7 +277,7 @@ struct Fitter {
   }
 
   // FP64 re-evaluation of s, q and Delta L at grid points ls[0..n), n <=
-  // kRescore, by the direct off-grid sums of Sec. IV-B/C on the FP64
+  // kRescore, by the direct off-grid sums of Sec. III-B/C on the FP64
   // generators (mixed paths: the FP32 grid only proposes candidates).
   __device__ void rescore(const int* ls, int n, double* dl_out, double* s_out, c128* q_out, int K) {
     for (int j = threadIdx.x; j < n; j += kNT) w.rs_theta[j] = (double)ls[j] / (double)L;
@@ -375,7 +375,7 @@ struct Fitter {
   }
 
   // ---------------------------------------------- approximate activation ---
-  // One pass of the scheme of Sec. III-E.  Returns the number activated.
+  // One pass of the scheme of Sec. II-E.  Returns the number activated.
   __device__ int approximate_activation(bool& grid_valid) {
     grid_valid = false;
     if (sh->zeta <= 0.0 || sh->K >= N) return 0;
@@ -651,7 +651,7 @@ struct Fitter {
       }
       if (sh->status != kST_OK) break;
       // step 2: zeta (eq. zetaUpdate)
-      // step 3: beta (eq. betaUpdate with the Woodbury forms of Sec. III-C3)
+      // step 3: beta (eq. betaUpdate with the Woodbury forms of Sec. II-C3)
       {
         const int K = sh->K;
         const double inv_delta = 1.0 / sh->delta_last;

@@ -1,4 +1,4 @@
-// lse_grid.cu -- grid evaluation of Sec. IV-D (Hansen, Fleury, Rao,
+// lse_grid.cu -- grid evaluation of Sec. III-D (Hansen, Fleury, Rao,
 // "Superfast Line Spectral Estimation"): for a given state (theta, gamma,
 // beta) compute q(theta_l), s(theta_l) and their first and second
 // theta-derivatives at theta_l = l/L.
@@ -6,7 +6,7 @@
 // Two kernels:
 //  factor_kernel  one block per instance: first column of C, Levinson
 //                 recursion (Gohberg-Semencul generators rho, delta) and
-//                 x = C^{-1} y by FFT convolutions (Sec. IV-A, IV-B).
+//                 x = C^{-1} y by FFT convolutions (Sec. III-A, III-B).
 //  grid_kernel    the length-L spectra of index-weighted generators and the
 //                 pointwise combine.  With c = (N-2)/2 and
 //                   Q_a = DFT_L((n-c)^a rho_n),  X_a = DFT_L(n^a x_n)

@@ -55,7 +55,7 @@ class Stream:
 
 
 def wrap_distance(a, b):
-    """Wrap-around distance on [0,1): d(x,y) = min(|x-y|, 1-|x-y|) (Sec. III-E footnote)."""
+    """Wrap-around distance on [0,1): d(x,y) = min(|x-y|, 1-|x-y|) (Sec. II-E footnote)."""
     d = np.abs(np.asarray(a, dtype=np.float64) - np.asarray(b, dtype=np.float64)) % 1.0
     return np.minimum(d, 1.0 - d)
 
@@ -123,7 +123,7 @@ def make_instance(N: int, K: int, snr_db: float, seed: int, *, law: str = "cn",
 
 
 def default_grid_size(N: int) -> int:
-    """L = 8N rounded to the nearest power of two (Sec. III-D footnote)."""
+    """L = 8N rounded to the nearest power of two (Sec. II-D footnote)."""
     return 1 << int(round(math.log2(8 * N)))
 
 
@@ -190,5 +190,5 @@ def make_request(spec):
 
 
 def paper_accuracy_n128(trial: int, seed0: int = 601):
-    """N=128, K=10, 20 dB, the paper's amplitude law (Sec. VI-A, Fig. 3)."""
+    """N=128, K=10, 20 dB, the paper's amplitude law (Sec. VI-A, Fig. 2)."""
     return make_instance(128, 10, 20.0, seed0 + trial, law="paper"), 1024

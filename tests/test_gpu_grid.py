@@ -1,4 +1,4 @@
-"""GPU grid evaluation (Sec. IV-D) through the C ABI against the dense FP64
+"""GPU grid evaluation (Sec. III-D) through the C ABI against the dense FP64
 oracle, element by element.
 
 Tolerances: FP64 path 1e-8 normwise (and 1e-8 pointwise for s): the

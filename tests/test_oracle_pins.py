@@ -42,7 +42,7 @@ def test_unit_phase_exact_reduction():
 
 
 def test_covariance_is_hermitian_toeplitz_with_first_column():
-    """C of eq. (py) is Hermitian Toeplitz and its first column is c_m (Sec. IV)."""
+    """C of eq. (py) is Hermitian Toeplitz and its first column is c_m (Sec. III)."""
     y, th, g, b = rand_state(17, 4, 1)
     C = dn.covariance(17, th, g, b)
     c = dn.first_column(17, th, g, b)
@@ -121,7 +121,7 @@ def test_gohberg_semencul_reproduces_inverse(N):
     Ci = (T1.conj().T @ T1 - T0 @ T0.conj().T) / delta[-1]
     ref = np.linalg.inv(ev.C)
     assert np.abs(Ci - ref).max() < 1e-10 * np.abs(ref).max()
-    # the pivots give the log-determinant (Sec. IV-A)
+    # the pivots give the log-determinant (Sec. III-A)
     assert abs(np.sum(np.log(delta)) - np.linalg.slogdet(ev.C)[1]) < 1e-10 * N
 
 
@@ -328,7 +328,7 @@ def _nmse_db(inst, r):
 
 @pytest.mark.slow
 def test_accuracy_near_paper_at_20db():
-    """Statistical pin: BSR, CSR, NMSE of Sec. VI-B (Fig. 3) at N=128, K=10, 20 dB."""
+    """Statistical pin: BSR, CSR, NMSE of Sec. VI-C (Fig. 2) at N=128, K=10, 20 dB."""
     from scipy.optimize import linear_sum_assignment
     gold = json.load(open(os.path.join(HERE, "golden", "paper_accuracy_n128.json")))["points"]["20"]
     trials = 40
