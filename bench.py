@@ -203,6 +203,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--batch", type=int, default=B, help="instances per step (smaller cases for profiling)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-API end-to-end leg")
+    ap.add_argument("--paths", default="mixed_df,mixed,fp64",
+                    help="comma list of precision paths to time (the first is the headline)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -277,9 +279,10 @@ def main():
         return float(t.item())
 
     res = {}
-    paths = [("mixed_df", lse.LSE_PREC_MIXED_DF), ("mixed", lse.LSE_PREC_MIXED)] + \
-        ([] if args.no_fp64 else [("fp64", lse.LSE_PREC_FP64)])
-    HEAD = "mixed_df"
+    precs = {"mixed_df": lse.LSE_PREC_MIXED_DF, "mixed": lse.LSE_PREC_MIXED, "fp64": lse.LSE_PREC_FP64}
+    names = [p for p in args.paths.split(",") if p and not (args.no_fp64 and p == "fp64")]
+    paths = [(p, precs[p]) for p in names]
+    HEAD = names[0]
     ctxs = {}
     for name, prec in paths:
         ctx = lse.lse_create(lse.lse_config_default(device=local, precision=prec, grid_size=L))
