@@ -78,8 +78,16 @@ typedef struct lse_config {
   int32_t max_inner;               /* (theta,gamma) updates per outer iteration (Sec. II-D): 5 */
   int32_t approx_activation_iters; /* outer iterations that may use the approximate activation
                                       of Sec. II-E; default 10; 0 disables it */
-  uint64_t flags;                  /* reserved, must be 0 */
+  uint64_t flags;                  /* LSE_FLAG_* bits; other bits must be 0 */
 } lse_config;
+
+/* Disable the grid-FFT autotuner.  By default the first grid evaluation of a
+ * context for a new (element type, L) times every on-chip FFT schedule on that
+ * batch (this synchronises the stream once) and keeps the fastest; with the
+ * environment variable LSE_AUTOTUNE_CACHE naming a file, choices are loaded
+ * at lse_create and saved after tuning.  Tune (or load the cache) before
+ * capturing grid evaluations into a CUDA graph. */
+#define LSE_FLAG_NO_AUTOTUNE 1u
 
 /* Fill cfg with the paper's defaults (device 0, FP64, tau = 5, ...). */
 LSE_API void lse_config_default(lse_config* cfg);

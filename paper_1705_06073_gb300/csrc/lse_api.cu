@@ -3,8 +3,11 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/lse.h"
@@ -34,12 +37,14 @@ struct lse_ctx {
   c128* tw64 = nullptr;
   c64* tw32 = nullptr;
   int log2max = 0;
-  DevBuf ws, desc, counter, stage_in, stage_out, fac;
+  DevBuf ws, desc, counter, stage_in, stage_out, fac, tasks;
   size_t allocated = 0;
   InstDesc* h_desc = nullptr;  // pinned
   size_t h_desc_cap = 0;
   std::vector<TimedLaunch> timed[3];
   std::string err;
+  // autotuned schedule of the on-chip grid FFT per (FP32?, L)
+  std::map<std::pair<int, int>, int> grid_variant;
 };
 
 namespace {
@@ -151,6 +156,32 @@ void record(lse_ctx* c, int which, cudaStream_t st, bool start) {
   }
 }
 
+// Autotune cache file: lines "grid <f32|f64> <L> <variant>".
+const char* autotune_path() { return std::getenv("LSE_AUTOTUNE_CACHE"); }
+
+void load_autotune(lse_ctx* c) {
+  const char* path = autotune_path();
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char kind[16], dt[8];
+  int L, v;
+  while (std::fscanf(f, "%15s %7s %d %d", kind, dt, &L, &v) == 4)
+    if (!std::strcmp(kind, "grid") && v >= 0 && v < grid_variant_count())
+      c->grid_variant[{std::strcmp(dt, "f32") == 0 ? 1 : 0, L}] = v;
+  std::fclose(f);
+}
+
+void save_autotune(const lse_ctx* c) {
+  const char* path = autotune_path();
+  if (!path) return;
+  FILE* f = std::fopen(path, "w");
+  if (!f) return;
+  for (const auto& kv : c->grid_variant)
+    std::fprintf(f, "grid %s %d %d\n", kv.first.first ? "f32" : "f64", kv.first.second, kv.second);
+  std::fclose(f);
+}
+
 }  // namespace
 
 extern "C" {
@@ -192,7 +223,8 @@ lse_status lse_create(const lse_config* cfg, lse_ctx** out) {
   if (cfg) c = *cfg; else lse_config_default(&c);
   if (c.precision != LSE_PREC_FP64 && c.precision != LSE_PREC_MIXED && c.precision != LSE_PREC_MIXED_DF)
     return LSE_EINVAL;
-  if (c.max_outer < 1 || c.max_inner < 0 || c.approx_activation_iters < 0 || !(c.tau >= 0.0) || c.flags)
+  if (c.max_outer < 1 || c.max_inner < 0 || c.approx_activation_iters < 0 || !(c.tau >= 0.0) ||
+      (c.flags & ~(uint64_t)LSE_FLAG_NO_AUTOTUNE))
     return LSE_EINVAL;
   if (c.grid_size < 0 || (c.grid_size > 0 && !is_pow2(c.grid_size))) return LSE_EINVAL;
   int ndev = 0;
@@ -205,6 +237,7 @@ lse_status lse_create(const lse_config* cfg, lse_ctx** out) {
     delete ctx;
     return LSE_ECUDA;
   }
+  load_autotune(ctx);
   lse_status s = ensure_tables(ctx, 17);
   if (s == LSE_OK) s = ensure(ctx, ctx->counter, 256);
   if (s != LSE_OK) {
@@ -219,7 +252,7 @@ void lse_destroy(lse_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->cfg.device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  for (DevBuf* b : {&ctx->ws, &ctx->desc, &ctx->counter, &ctx->stage_in, &ctx->stage_out, &ctx->fac})
+  for (DevBuf* b : {&ctx->ws, &ctx->desc, &ctx->counter, &ctx->stage_in, &ctx->stage_out, &ctx->fac, &ctx->tasks})
     if (b->p) cudaFree(b->p);
   if (ctx->tw64) cudaFree(ctx->tw64);
   if (ctx->tw32) cudaFree(ctx->tw32);
@@ -404,7 +437,8 @@ lse_status lse_eval_grid_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* 
   const size_t fws = factor_workspace_bytes(Nmax) * B;
   const size_t gws_hdr = ((size_t)B * sizeof(int64_t) + 255) & ~size_t(255);
   const size_t gws = grid_workspace_bytes(B, g, f32);
-  const size_t fac_bytes = (size_t)totN * 2 * sizeof(c128) + (size_t)B * (sizeof(double) + sizeof(int)) + 512;
+  const size_t fac_bytes =
+      (size_t)totN * (4 * sizeof(c128) + 3 * sizeof(c64)) + (size_t)B * (sizeof(double) + sizeof(int)) + 1024;
   if ((sst = ensure(ctx, ctx->ws, std::max(fws, gws_hdr + gws)))) return sst;
   if ((sst = ensure(ctx, ctx->fac, fac_bytes))) return sst;
   if ((sst = stage_desc(ctx, d))) return sst;
@@ -424,18 +458,57 @@ lse_status lse_eval_grid_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* 
   }
   c128* rho = (c128*)ctx->fac.p;
   c128* x = rho + totN;
-  double* delta = (double*)(x + totN);
+  c128* omega = x + totN;  // 2N per instance (2N-1 used)
+  double* delta = (double*)(omega + 2 * totN);
   int* status = (int*)(delta + B);
+  c64* omega32 = (c64*)(((uintptr_t)(status + B) + 255) & ~(uintptr_t)255);
+  c64* x32 = omega32 + 2 * totN;
   record(ctx, 1, st, true);
   cudaError_t e = launch_factor(ctx->cfg.precision == LSE_PREC_MIXED_DF, y_d, (const InstDesc*)ctx->desc.p, B, Nmax, theta_d, gamma_d, beta_d, tables(ctx),
-                                ctx->ws.p, rho, x, delta, status, st);
+                                ctx->ws.p, rho, x, omega, omega32, x32, delta, status, st);
   record(ctx, 1, st, false);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "factor kernel launch");
   // the grid kernel reuses the workspace; its offset table goes first
   LSE_CUDA(ctx, cudaMemcpyAsync(ctx->ws.p, woff.data(), B * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  // task list of the on-chip grid kernel
+  std::vector<int4> tasks(5 * (size_t)B);
+  const int ntasks = grid_tasks(d.data(), B, q, dq, d2q, s, ds, d2s, tasks.data());
+  if ((sst = ensure(ctx, ctx->tasks, std::max<size_t>(1, ntasks) * sizeof(int4)))) return sst;
+  LSE_CUDA(ctx, cudaMemcpyAsync(ctx->tasks.p, tasks.data(), ntasks * sizeof(int4), cudaMemcpyHostToDevice, st));
+  LSE_CUDA(ctx, cudaStreamSynchronize(st));  // the host task vector goes out of scope
+  // schedule of the on-chip grid FFT: cached, or tuned now on this batch
+  int variant = 1;
+  if (grid_on_chip(f32, Lmax)) {
+    const auto key = std::make_pair(f32 ? 1 : 0, Lmax);
+    auto it = ctx->grid_variant.find(key);
+    if (it != ctx->grid_variant.end()) {
+      variant = it->second;
+    } else if (!(ctx->cfg.flags & LSE_FLAG_NO_AUTOTUNE)) {
+      const int nv = grid_variant_count();
+      std::vector<cudaEvent_t> ev(nv + 1);
+      for (auto& x : ev) LSE_CUDA(ctx, cudaEventCreate(&x));
+      cudaEventRecord(ev[0], st);
+      for (int v = 0; v < nv; ++v) {
+        e = launch_grid(v, f32, (const InstDesc*)ctx->desc.p, B, Lmax, rho, x, omega, x32, omega32, delta,
+                        tables(ctx), ctx->ws.p, (const int4*)ctx->tasks.p, ntasks, q, dq, d2q, s, ds, d2s, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "grid kernel launch (autotune)");
+        cudaEventRecord(ev[v + 1], st);
+      }
+      LSE_CUDA(ctx, cudaEventSynchronize(ev[nv]));
+      float best = 1e30f;
+      for (int v = 0; v < nv; ++v) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[v], ev[v + 1]);
+        if (ms < best) { best = ms; variant = v; }
+      }
+      for (auto& x : ev) cudaEventDestroy(x);
+      ctx->grid_variant[key] = variant;
+      save_autotune(ctx);
+    }
+  }
   record(ctx, 2, st, true);
-  e = launch_grid(f32, (const InstDesc*)ctx->desc.p, B, Lmax, rho, x, delta, tables(ctx), ctx->ws.p, q, dq, d2q, s,
-                  ds, d2s, st);
+  e = launch_grid(variant, f32, (const InstDesc*)ctx->desc.p, B, Lmax, rho, x, omega, x32, omega32, delta,
+                  tables(ctx), ctx->ws.p, (const int4*)ctx->tasks.p, ntasks, q, dq, d2q, s, ds, d2s, st);
   record(ctx, 2, st, false);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "grid kernel launch");
   if (st != ctx->stream) {
@@ -492,7 +565,7 @@ lse_status lse_eval_grid(lse_ctx* ctx, const float* y, int32_t N, const double* 
   for (int i = 0; i < 6; ++i)
     if (host[i]) LSE_CUDA(ctx, cudaMemcpyAsync(host[i], dev[i], sz[i], cudaMemcpyDeviceToHost, ctx->stream));
   int fst = 0;
-  const int* status = (const int*)((double*)((c128*)ctx->fac.p + 2 * (size_t)N) + 1);
+  const int* status = (const int*)((double*)((c128*)ctx->fac.p + 4 * (size_t)N) + 1);
   LSE_CUDA(ctx, cudaMemcpyAsync(&fst, status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   LSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (fst) return fail(ctx, LSE_ENUMERIC, "Levinson recursion broke down");

@@ -18,6 +18,7 @@
 //                 (d = delta_{N-1}; DFT_L(v)(l) = sum_n v_n e^{-j 2 pi n l / L}).
 #include "lse_device.cuh"
 #include "lse_df64.cuh"
+#include "lse_fft_smem.cuh"
 #include "lse_internal.h"
 
 namespace lse {
@@ -50,7 +51,7 @@ template <bool DF>
 __global__ void __launch_bounds__(factor_threads<DF>(), 1)
     factor_kernel(const float* y, const InstDesc* inst, int Nmax, const double* theta, const double* gamma,
                   const double* beta, Tables tab, char* ws, size_t ws_bytes, c128* rho_out, c128* x_out,
-                  double* delta_out, int* status) {
+                  c128* omega_out, c64* omega32_out, c64* x32_out, double* delta_out, int* status) {
   constexpr int kFNT = factor_threads<DF>();
   __shared__ c128 red[kFNT];
   __shared__ LevShared lev;
@@ -95,6 +96,33 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
   block_fft<kFNT, double>([=] __device__(int i) { return i < N ? yv[i] : zero<double>(); }, Yf, bufs[4], log2M2, false,
                           tw);
   block_gs_apply<kFNT>(rho, Yf, x, N, log2M2, lr.delta_last, bufs, tw);
+  // Diagonal sums of C^{-1} (Sec. III-C, Appendix B):
+  //   omega_s(i) = (1/d) sum_q [(q-c) + (q+i-c)] rho_q conj(rho_{q+i}),  |i| < N,
+  // two cross-correlations; with P = FFT(rho) (still in bufs[0] after the
+  // Gohberg-Semencul apply) and Pw = FFT((n-c) rho_n):
+  //   omega_s(i) = IFFT(2 Re(Pw conj(P)))(-i) / (d M2).
+  {
+    const double cen = 0.5 * (double)(N - 2);
+    const c128* P = bufs[0];
+    c128* Pw = bufs[1];
+    c128* G = bufs[2];
+    block_fft<kFNT, double>([=] __device__(int i) { return i < N ? ((double)i - cen) * rho[i] : zero<double>(); }, Pw,
+                            bufs[4], log2M2, false, tw);
+    block_fft<kFNT, double>([=] __device__(int k) { return mk(2.0 * (Pw[k] * conj(P[k])).re, 0.0); }, G, bufs[4],
+                            log2M2, true, tw);
+    const double sc = 1.0 / (lr.delta_last * (double)(1 << log2M2));
+    const int msk = (1 << log2M2) - 1;
+    c128* om = omega_out + 2 * d.y_off;
+    c64* om32 = omega32_out + 2 * d.y_off;
+    for (int i = (int)threadIdx.x - (N - 1); i <= N - 1; i += kFNT) {
+      const c128 v = sc * G[(-i) & msk];
+      om[i + N - 1] = v;
+      om32[i + N - 1] = cvt<float>(v);
+    }
+    c64* x32 = x32_out + d.y_off;
+    for (int n = threadIdx.x; n < N; n += kFNT) x32[n] = cvt<float>(x[n]);
+    __syncthreads();
+  }
   if (threadIdx.x == 0) { status[b] = 0; delta_out[b] = lr.delta_last; }
 }
 
@@ -159,6 +187,92 @@ __global__ void __launch_bounds__(kFNT, 1)
   }
 }
 
+
+// ------------------------------------------------------- grid (on chip) ---
+// Grid outputs as five independent length-L FFTs, each done by one block in
+// shared memory (lse_fft_smem.cuh):
+//   job 0: Z = sum_i (1 - i/N) omega_s(i) e^{+j2pi i l/L} -> s = Re Z, s' = 2 pi N Im Z
+//          (s and s'/(2 pi N) are real transforms of Hermitian sequences and
+//          share one complex FFT; the 1/(2 pi N) keeps both parts the same size)
+//   job 1: s'' = Re sum_i (-4 pi^2 i^2) omega_s(i) e^{+j2pi i l/L}
+//   jobs 2-4: q^(a) = sum_n (-j 2 pi n)^a x_n e^{-j2pi n l/L}, a = 0, 1, 2
+// (Sec. III-D: the grid vectors are FFTs; omega_s from the factor kernel.)
+template <class T>
+struct GridPtrs {
+  T *q, *dq, *d2q, *s, *ds, *d2s;
+};
+
+template <class T>
+__host__ __device__ constexpr int grid_mmax() { return sizeof(T) == 4 ? 16384 : 8192; }
+
+template <class T, int NT, bool R16>
+__global__ void __launch_bounds__(NT)
+    grid_fft_kernel(const InstDesc* inst, const cx<T>* omega_all, const cx<T>* x_all, Tables tab, GridPtrs<T> out,
+                    const int4* tasks) {
+  extern __shared__ __align__(16) char gsm[];
+  // task: x = instance, y = job, z = partner instance of a paired s'' job (or -1)
+  const int4 task = tasks[blockIdx.x];
+  const int b = task.x, job = task.y, b2 = task.z;
+  const InstDesc d = inst[b];
+  const int N = d.N, L = d.L, log2L = ilog2((uint32_t)L);
+  const int64_t g = d.g_off;
+  cx<T>* sm = (cx<T>*)gsm;
+  cx<T>* tlo = sm + L + (L >> 4);
+  cx<T>* thi = tlo + (1 << ((log2L + 1) >> 1));
+  const cx<T>* gtw = (const cx<T>*)(sizeof(T) == 8 ? (const void*)tab.tw64 : (const void*)tab.tw32);
+  const SmemTwiddles<T> tw = make_smem_twiddles<NT, T>(tlo, thi, log2L, gtw, tab.log2max);
+  constexpr int MMAX = grid_mmax<T>();
+  // one FFT instantiation for every job (the job only changes the input
+  // functor, the direction and the epilogue) keeps the kernel's code small
+  const cx<T>* om = omega_all + 2 * d.y_off + (N - 1);  // om[i], |i| < N
+  // a paired s'' job also transforms a second instance of the same N and L in
+  // the imaginary part (both inputs are Hermitian, both outputs real)
+  const cx<T>* om2 = b2 >= 0 ? omega_all + 2 * inst[b2].y_off + (N - 1) : om;
+  const int64_t g2 = b2 >= 0 ? inst[b2].g_off : 0;
+  const cx<T>* x = x_all + d.y_off;
+  // scalars in the element type: the FP64 pipe is slow enough that a per-
+  // thread FP64 division showed up in the profile
+  const T invN = (T)1 / (T)N;
+  const T fpp = (T)(-4.0 * kPi * kPi);
+  const T tp = (T)kTwoPi;
+  auto gen = [=] __device__(int l) {
+    cx<T> v = zero<T>();
+    if (job <= 1) {
+      const int i = l < N ? l : l - L;  // lag stored at l = i mod L
+      if (i > -N && i < N) {
+        const cx<T> o = om[i];
+        const T fi = (T)i;
+        if (job == 0) {
+          v = ((T)1 - fi * invN) * o;
+        } else {
+          v = (fpp * fi * fi) * o;
+          if (b2 >= 0) v = v + mul_j((fpp * fi * fi) * om2[i]);
+        }
+      }
+    } else if (l < N) {
+      const T w = tp * (T)l;
+      v = x[l];
+      if (job == 3) v = mk(w * v.im, -w * v.re);  // -j w x
+      if (job == 4) v = (-w * w) * v;
+    }
+    return v;
+  };
+  T* o0 = job == 0 ? out.s : job == 1 ? out.d2s : job == 2 ? out.q : job == 3 ? out.dq : out.d2q;
+  T* o1 = job == 0 ? out.ds : (b2 >= 0 ? out.d2s : nullptr);
+  const T f = job == 0 ? tp * (T)N : (T)1;
+  const int64_t go = job == 0 ? g : g2;
+  auto epi = [=] __device__(int l, cx<T> z) {
+    if (job >= 2) {
+      ((cx<T>*)o0)[g + l] = z;
+    } else {
+      if (o0) o0[g + l] = z.re;
+      if (o1) o1[go + l] = f * z.im;
+    }
+  };
+  __syncthreads();  // twiddle tables
+  smem_fft_run<NT, MMAX, R16, T>(gen, sm, log2L, job <= 1, tw, epi);
+}
+
 }  // namespace
 
 size_t factor_workspace_bytes(int Nmax) { return factor_layout(Nmax).total; }
@@ -166,22 +280,25 @@ size_t factor_workspace_bytes(int Nmax) { return factor_layout(Nmax).total; }
 template <bool DF>
 static cudaError_t launch_factor_t(const float* y, const InstDesc* inst, int B, int Nmax, const double* theta,
                                    const double* gamma, const double* beta, const Tables& tab, void* ws,
-                                   c128* rho_out, c128* x_out, double* delta_out, int* status, cudaStream_t stream) {
+                                   c128* rho_out, c128* x_out, c128* omega_out, c64* omega32_out, c64* x32_out,
+                                   double* delta_out, int* status, cudaStream_t stream) {
   const int smem = 200 * 1024;
   cudaError_t e = cudaFuncSetAttribute(factor_kernel<DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   factor_kernel<DF><<<B, factor_threads<DF>(), smem, stream>>>(y, inst, Nmax, theta, gamma, beta, tab, (char*)ws,
-                                               factor_workspace_bytes(Nmax), rho_out, x_out, delta_out, status);
+                                               factor_workspace_bytes(Nmax), rho_out, x_out, omega_out,
+                                               omega32_out, x32_out, delta_out, status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_factor(bool df, const float* y, const InstDesc* inst, int B, int Nmax, const double* theta,
                           const double* gamma, const double* beta, const Tables& tab, void* ws, c128* rho_out,
-                          c128* x_out, double* delta_out, int* status, cudaStream_t stream) {
-  return df ? launch_factor_t<true>(y, inst, B, Nmax, theta, gamma, beta, tab, ws, rho_out, x_out, delta_out,
-                                    status, stream)
-            : launch_factor_t<false>(y, inst, B, Nmax, theta, gamma, beta, tab, ws, rho_out, x_out, delta_out,
-                                     status, stream);
+                          c128* x_out, c128* omega_out, c64* omega32_out, c64* x32_out, double* delta_out,
+                          int* status, cudaStream_t stream) {
+  return df ? launch_factor_t<true>(y, inst, B, Nmax, theta, gamma, beta, tab, ws, rho_out, x_out, omega_out,
+                                    omega32_out, x32_out, delta_out, status, stream)
+            : launch_factor_t<false>(y, inst, B, Nmax, theta, gamma, beta, tab, ws, rho_out, x_out, omega_out,
+                                     omega32_out, x32_out, delta_out, status, stream);
 }
 
 size_t grid_workspace_bytes(int B, int64_t total_L, bool f32) {
@@ -189,10 +306,71 @@ size_t grid_workspace_bytes(int B, int64_t total_L, bool f32) {
   return (size_t)total_L * 2 * 5 * (f32 ? sizeof(c64) : sizeof(c128));
 }
 
-cudaError_t launch_grid(bool f32, const InstDesc* inst, int B, int Lmax, const c128* rho, const c128* x,
-                        const double* delta, const Tables& tab, void* ws, void* q, void* dq, void* d2q, void* s,
-                        void* ds, void* d2s, cudaStream_t stream) {
-  (void)Lmax;
+// Schedules of the on-chip grid FFT: (threads per block, radix-16 passes).
+// The autotuner in lse_api.cu times them on the live batch and keeps the
+// fastest per (element type, grid size).
+static const GridVariant kGridVariants[] = {{256, true}, {512, true}, {1024, true}, {512, false}};
+int grid_variant_count() { return (int)(sizeof(kGridVariants) / sizeof(kGridVariants[0])); }
+GridVariant grid_variant(int i) { return kGridVariants[i]; }
+
+template <class T, int NT, bool R16>
+static cudaError_t launch_grid_fft_v(const InstDesc* inst, const int4* tasks, int ntasks, const cx<T>* omega,
+                                     const cx<T>* x, const Tables& tab, int Lmax, const GridPtrs<T>& o,
+                                     cudaStream_t stream) {
+  const int smem = (int)smem_fft_bytes(ilog2((uint32_t)Lmax), sizeof(cx<T>));
+  cudaError_t e = cudaFuncSetAttribute(grid_fft_kernel<T, NT, R16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  grid_fft_kernel<T, NT, R16><<<ntasks, NT, smem, stream>>>(inst, omega, x, tab, o, tasks);
+  return cudaGetLastError();
+}
+
+template <class T>
+static cudaError_t launch_grid_fft(int variant, const InstDesc* inst, const int4* tasks, int ntasks,
+                                   const cx<T>* omega, const cx<T>* x, const Tables& tab, int Lmax, void* q, void* dq,
+                                   void* d2q, void* s, void* ds, void* d2s, cudaStream_t stream) {
+  if (!ntasks) return cudaSuccess;
+  const GridPtrs<T> o{(T*)q, (T*)dq, (T*)d2q, (T*)s, (T*)ds, (T*)d2s};
+  switch (variant) {
+    case 0: return launch_grid_fft_v<T, 256, true>(inst, tasks, ntasks, omega, x, tab, Lmax, o, stream);
+    case 1: return launch_grid_fft_v<T, 512, true>(inst, tasks, ntasks, omega, x, tab, Lmax, o, stream);
+    case 2: return launch_grid_fft_v<T, 1024, true>(inst, tasks, ntasks, omega, x, tab, Lmax, o, stream);
+    default: return launch_grid_fft_v<T, 512, false>(inst, tasks, ntasks, omega, x, tab, Lmax, o, stream);
+  }
+}
+
+int grid_tasks(const InstDesc* inst, int B, bool q, bool dq, bool d2q, bool s, bool ds, bool d2s, int4* out) {
+  int n = 0;
+  int pend = -1;  // an instance whose s'' job waits for a partner of the same N and L
+  for (int b = 0; b < B; ++b) {
+    if (s || ds) out[n++] = make_int4(b, 0, -1, 0);
+    if (q) out[n++] = make_int4(b, 2, -1, 0);
+    if (dq) out[n++] = make_int4(b, 3, -1, 0);
+    if (d2q) out[n++] = make_int4(b, 4, -1, 0);
+    if (d2s) {
+      if (pend >= 0 && inst[pend].N == inst[b].N && inst[pend].L == inst[b].L) {
+        out[n++] = make_int4(pend, 1, b, 0);
+        pend = -1;
+      } else {
+        if (pend >= 0) out[n++] = make_int4(pend, 1, -1, 0);
+        pend = b;
+      }
+    }
+  }
+  if (pend >= 0) out[n++] = make_int4(pend, 1, -1, 0);
+  return n;
+}
+
+bool grid_on_chip(bool f32, int Lmax) { return Lmax <= (f32 ? grid_mmax<float>() : grid_mmax<double>()); }
+
+cudaError_t launch_grid(int variant, bool f32, const InstDesc* inst, int B, int Lmax, const c128* rho, const c128* x,
+                        const c128* omega, const c64* x32, const c64* omega32, const double* delta, const Tables& tab,
+                        void* ws, const int4* tasks, int ntasks, void* q, void* dq, void* d2q, void* s, void* ds,
+                        void* d2s, cudaStream_t stream) {
+  if (grid_on_chip(f32, Lmax))
+    return f32 ? launch_grid_fft<float>(variant, inst, tasks, ntasks, omega32, x32, tab, Lmax, q, dq, d2q, s, ds, d2s,
+                                        stream)
+               : launch_grid_fft<double>(variant, inst, tasks, ntasks, omega, x, tab, Lmax, q, dq, d2q, s, ds, d2s,
+                                         stream);
   // ws begins with B int64 offsets (per instance, bytes) followed by buffers
   const int64_t* ws_off = (const int64_t*)ws;
   char* base = (char*)ws;

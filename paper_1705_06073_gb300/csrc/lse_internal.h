@@ -60,11 +60,29 @@ cudaError_t launch_fit(int prec, const float* y, const InstDesc* inst, int B, in
 size_t factor_workspace_bytes(int Nmax);
 cudaError_t launch_factor(bool df, const float* y, const InstDesc* inst, int B, int Nmax, const double* theta,
                           const double* gamma, const double* beta, const Tables& tab, void* ws, c128* rho_out,
-                          c128* x_out, double* delta_out, int* status, cudaStream_t stream);
+                          c128* x_out, c128* omega_out, c64* omega32_out, c64* x32_out, double* delta_out,
+                          int* status, cudaStream_t stream);
 // Eval-grid: spectra and combine.  outputs in T (float for mixed, double for fp64).
-cudaError_t launch_grid(bool f32, const InstDesc* inst, int B, int Lmax, const c128* rho, const c128* x,
-                        const double* delta, const Tables& tab, void* ws, void* q, void* dq, void* d2q, void* s,
-                        void* ds, void* d2s, cudaStream_t stream);
+// Schedule of the on-chip grid FFT kernel.
+struct GridVariant {
+  int threads;
+  bool radix16;
+};
+int grid_variant_count();
+GridVariant grid_variant(int i);
+
+// rho, x: [sum N]; omega: instance b's 2N-1 diagonal sums at 2*y_off.
+// variant: index of the on-chip schedule (ignored for grids too large for it).
+cudaError_t launch_grid(int variant, bool f32, const InstDesc* inst, int B, int Lmax, const c128* rho, const c128* x,
+                        const c128* omega, const c64* x32, const c64* omega32, const double* delta, const Tables& tab,
+                        void* ws, const int4* tasks, int ntasks, void* q, void* dq, void* d2q, void* s, void* ds,
+                        void* d2s, cudaStream_t stream);
+// The on-chip grid kernel's task list for a batch (host): one block per
+// (instance, output family); the s'' transforms of consecutive instances of
+// equal N and L share one block.  `out` needs 5 B entries; returns the count.
+int grid_tasks(const InstDesc* inst, int B, bool q, bool dq, bool d2q, bool s, bool ds, bool d2s, int4* out);
+// true when every grid of the batch fits the on-chip FFT kernel (no workspace needed)
+bool grid_on_chip(bool f32, int Lmax);
 size_t grid_workspace_bytes(int B, int64_t total_L, bool f32);
 
 }  // namespace lse
