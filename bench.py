@@ -192,6 +192,80 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ serving ---
+def serve_leg(lse, seconds, device):
+    """Continuous batching under Poisson arrivals at 2000 req/s with the
+    serving-stream size mix (N log-uniform on [256, 32768], K uniform on
+    [4, N/32], SNR uniform on [5, 25] dB), 40 GB device-memory budget.
+    Latency = submit -> result returned by poll, wall clock."""
+    import time as _t
+    from paper_1705_06073_gb300 import synth
+    times, specs = synth.serving_stream(2000.0, seconds, seed=501)
+    reqs = [synth.make_request(sp)[0].y for sp in specs]
+    cfg = lse.lse_config_default(device=device, precision=lse.LSE_PREC_MIXED_DF, hbm_budget_bytes=40 << 30)
+    srv = lse.Server(cfg, streams=8, max_group=19, K_cap=32768)
+    sub, fin = {}, {}
+    try:
+        t0 = _t.perf_counter()
+        i = 0
+        while len(fin) < len(reqs):
+            now = _t.perf_counter() - t0
+            while i < len(reqs) and times[i] <= now:
+                srv.submit(reqs[i], i)
+                sub[i] = _t.perf_counter() - t0
+                i += 1
+            for r in srv.poll():
+                fin[r["request_id"]] = (_t.perf_counter() - t0, r["status"])
+            if now > 600:
+                break
+        wall = _t.perf_counter() - t0
+    finally:
+        srv.close()
+    import numpy as _np
+    lat = _np.array([fin[k][0] - sub[k] for k in fin]) * 1e3
+    ns = _np.array([len(y) for y in reqs])
+    return {"offered_rate_per_s": 2000.0, "arrival_window_s": seconds, "requests": len(reqs),
+            "completed": len(fin), "failed": int(sum(1 for v in fin.values() if v[1] not in (0, 5))),
+            "p50_ms": float(_np.percentile(lat, 50)), "p99_ms": float(_np.percentile(lat, 99)),
+            "max_ms": float(lat.max()), "completed_per_s": len(fin) / wall, "wall_s": wall,
+            "n_median": int(_np.median(ns)), "n_max": int(ns.max()),
+            "note": "2000 req/s with N up to 32768 exceeds the device's capacity (the O(N^2) recursion "
+                    "runs once per evaluation); latency includes the queueing that follows"}
+
+
+def ragged_leg(lse, dev):
+    """1024 instances, N uniform on [128, 8192], K = max(1, N/64), one planned
+    launch replayed as a CUDA graph (longest instances first)."""
+    import numpy as _np
+    import torch as _torch
+    from paper_1705_06073_gb300 import synth
+    insts = synth.ragged1024()
+    ys = [i.y for i, _ in insts]
+    offs = _np.concatenate([[0], _np.cumsum([len(y) for y in ys])]).astype(_np.int64)
+    y_d = _torch.from_numpy(_np.concatenate(ys)).to(dev)
+    ctx = lse.lse_create(lse.lse_config_default(device=dev.index or 0, precision=lse.LSE_PREC_MIXED_DF))
+    try:
+        plan = lse.lse_plan_fit(ctx, offs)
+        out = lse.alloc_batch_out(offs, device=dev)
+        st = _torch.cuda.Stream(device=dev)
+        lse.lse_plan_launch(plan, y_d, out, st, graph=True)  # capture + warm-up
+        st.synchronize()
+        e0 = _torch.cuda.Event(enable_timing=True)
+        e1 = _torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        lse.lse_plan_launch(plan, y_d, out, st, graph=True)
+        e1.record(st)
+        st.synchronize()
+        ms = e0.elapsed_time(e1)
+        status = out["status"].cpu().numpy()
+        lse.lse_plan_destroy(plan)
+    finally:
+        lse.lse_destroy(ctx)
+    return {"instances": len(ys), "ms": ms, "fitted_instances_per_s": len(ys) / (ms / 1e3),
+            "graph_launches": 1, "status_nonzero": int(_np.count_nonzero((status != 0) & (status != 5))),
+            "n_range": [int(min(len(y) for y in ys)), int(max(len(y) for y in ys))]}
+
+
 # -------------------------------------------------------------- GPU arm ---
 def main():
     ap = argparse.ArgumentParser()
@@ -205,6 +279,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-API end-to-end leg")
     ap.add_argument("--paths", default="mixed_df,mixed,fp64",
                     help="comma list of precision paths to time (the first is the headline)")
+    ap.add_argument("--serve-seconds", type=float, default=0.02,
+                    help="arrival window of the serving leg (Poisson, 2000 req/s); 0 skips it")
+    ap.add_argument("--no-ragged", action="store_true", help="skip the ragged 1024-instance graph launch")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -368,6 +445,9 @@ def main():
     for c in ctxs.values():
         lse.lse_destroy(c)
 
+    serving = serve_leg(lse, args.serve_seconds, local) if args.serve_seconds > 0 and rank == 0 else None
+    ragged = ragged_leg(lse, dev) if not args.no_ragged and rank == 0 else None
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -415,6 +495,8 @@ def main():
                           "factor_kernel_ms": gm["factor_ms"], "grid_kernel_ms": gm["grid_ms"],
                           "grid_kernel_hbm_gbs": Bn * grid_bytes(N, L, False) / (gm["grid_ms"] / 1e3) / 1e9},
         "cpu_baseline": cpu,
+        "serving": serving,
+        "ragged_graph": ragged,
     }
     if "fp64" in res:
         f = res["fp64"]

@@ -162,6 +162,83 @@ LSE_API lse_status lse_fit_batch(lse_ctx* ctx, const float* y, const int64_t* of
 LSE_API lse_status lse_fit_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* offsets, int32_t B,
                            const lse_batch_out* out, void* stream);
 
+/* ---- Planned batches and CUDA graphs ----------------------------------
+ * A plan fixes the shape of a batched fit (offsets, B) and owns its device
+ * workspace, so that a launch enqueues device work only (a counter reset and
+ * one persistent fit kernel that pulls instances, largest N first) and can be
+ * captured into a CUDA graph. */
+typedef struct lse_plan lse_plan;
+
+/* Prepare fits of B instances laid out as `offsets` (HOST, B+1 entries, as for
+ * lse_fit_batch) with the context's configuration.  Allocates the plan's
+ * workspace (counted against hbm_budget_bytes) and uploads the descriptors. */
+LSE_API lse_status lse_plan_fit(lse_ctx* ctx, const int64_t* offsets, int32_t B, lse_plan** out);
+
+/* Enqueue one batched fit of the planned shape on `stream` (cudaStream_t; NULL
+ * = legacy default stream): device pointers as for lse_fit_batch_d.  No host
+ * synchronisation and no allocation, so the call may be stream-captured.  One
+ * launch of a plan at a time: launches of the same plan share its workspace. */
+LSE_API lse_status lse_plan_launch(lse_plan* plan, const float* y_d, const lse_batch_out* out, void* stream);
+
+/* As lse_plan_launch, through a CUDA graph: the first call (and any call with
+ * different y_d / out pointers) captures the launch into a graph on the
+ * context's stream and instantiates it; every call then replays it on
+ * `stream` with one cudaGraphLaunch. */
+LSE_API lse_status lse_plan_graph_launch(lse_plan* plan, const float* y_d, const lse_batch_out* out, void* stream);
+
+/* Wait for the device, release the plan's graph and workspace.  NULL is accepted. */
+LSE_API void lse_plan_destroy(lse_plan* plan);
+
+/* ---- Serving: continuous batching ---------------------------------------
+ * A server owns `streams` slots (each a stream, a context and device
+ * buffers).  lse_serve_submit queues a request; lse_serve_poll (never
+ * blocks on the GPU) hands back finished results, then lets every idle slot
+ * take the oldest pending requests (at most max_group, and only as many as
+ * the remaining device-memory budget cfg->hbm_budget_bytes allows; 0 = no
+ * cap) and launch one batched fit over them.  Requests that arrive while
+ * other groups run start on free slots, so their work overlaps on the
+ * device.  Each instance is fitted by one thread block with the arithmetic of
+ * a lone lse_fit, so its result does not depend on the batch it ran in.
+ * Not thread-safe: one server per host thread. */
+typedef struct lse_server lse_server;
+
+typedef struct lse_serve_result {
+  int64_t request_id;  /* out: the id given to lse_serve_submit */
+  int32_t status;      /* out: lse_status of this request */
+  int32_t N;           /* out */
+  int32_t K;           /* out: number of components (written even if K > K_cap) */
+  int32_t K_cap;       /* in: capacity of theta, gamma (K_cap) and alpha (2*K_cap) */
+  double* theta;       /* in: caller array (may be NULL) */
+  double* gamma;       /* in: caller array (may be NULL) */
+  double* alpha;       /* in: caller array, complex interleaved (may be NULL) */
+  double beta;         /* out */
+  double objective;    /* out */
+  int32_t iters;       /* out */
+  int32_t n_evals;     /* out */
+} lse_serve_result;
+
+/* cfg: fit configuration and total device-memory budget (NULL = defaults). */
+LSE_API lse_status lse_serve_create(const lse_config* cfg, int32_t streams, int32_t max_group, lse_server** out);
+
+/* Queue a request: y HOST complex64 [2N], copied; 2 <= N <= 131072.
+ * LSE_EBUDGET if the request alone needs more device memory than the budget. */
+LSE_API lse_status lse_serve_submit(lse_server* s, const float* y, int32_t N, int64_t request_id);
+
+/* Harvest finished groups, admit pending requests, and write up to `cap`
+ * finished results into `results` (their K_cap/theta/gamma/alpha set by the
+ * caller; a result whose K exceeds K_cap gets status LSE_ECAPACITY).  Returns
+ * the number written (results may be NULL to discard), -1 on a NULL server. */
+LSE_API int32_t lse_serve_poll(lse_server* s, lse_serve_result* results, int32_t cap);
+
+/* Requests submitted and not yet returned by lse_serve_poll. */
+LSE_API int32_t lse_serve_in_flight(const lse_server* s);
+
+/* Device memory the running groups hold, in bytes (the budgeted quantity). */
+LSE_API uint64_t lse_serve_device_bytes(const lse_server* s);
+
+/* Wait for running groups and release everything.  NULL is accepted. */
+LSE_API void lse_serve_destroy(lse_server* s);
+
 /* Grid evaluation (Sec. III-D): for C = beta I + sum_k gamma_k psi(theta_k)
  * psi(theta_k)^H (eq. py), compute on theta_l = l/L, l = 0..L-1,
  *   q(theta) = psi(theta)^H C^{-1} y,   s(theta) = psi(theta)^H C^{-1} psi(theta)

@@ -29,6 +29,8 @@ struct DevBuf {
 
 }  // namespace
 
+struct lse_plan;
+
 struct lse_ctx {
   lse_config cfg;
   int sm_count = 0;
@@ -45,6 +47,16 @@ struct lse_ctx {
   std::string err;
   // autotuned schedule of the on-chip grid FFT per (FP32?, L)
   std::map<std::pair<int, int>, int> grid_variant;
+};
+
+struct lse_plan {
+  lse_ctx* ctx = nullptr;
+  int B = 0, Nmax = 0, Lmax = 0, grid = 0, prec = 0;
+  DevBuf desc, counter, ws;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const float* g_y = nullptr;  // arguments baked into the captured graph
+  lse_batch_out g_out{};
 };
 
 namespace {
@@ -182,7 +194,33 @@ void save_autotune(const lse_ctx* c) {
   std::fclose(f);
 }
 
+// Descriptors of a batched fit, in the order the instances are handed out:
+// largest N first (longest-processing-time order) so that a ragged batch does
+// not end waiting on a big instance started last.  idx keeps the result slot.
+lse_status plan_fit_descs(lse_ctx* ctx, const int64_t* offsets, int32_t B, std::vector<InstDesc>& d, int& Nmax,
+                          int& Lmax) {
+  if (B < 1 || !offsets) return fail(ctx, LSE_EINVAL, "null offsets or B < 1");
+  if (offsets[0] != 0) return fail(ctx, LSE_EINVAL, "offsets[0] must be 0");
+  d.resize(B);
+  Nmax = 0;
+  Lmax = 0;
+  for (int b = 0; b < B; ++b) {
+    const int64_t n = offsets[b + 1] - offsets[b];
+    if (n < 2 || n > (1 << 17)) return fail(ctx, LSE_EINVAL, "instance " + std::to_string(b) + ": N out of range");
+    const int N = (int)n;
+    const int L = ctx->cfg.grid_size ? ctx->cfg.grid_size : default_L(N);
+    if (L < 2 * N) return fail(ctx, LSE_EINVAL, "grid size L must be >= 2N");
+    d[b] = InstDesc{offsets[b], N, L, 0, 0, b, 0};
+    Nmax = std::max(Nmax, N);
+    Lmax = std::max(Lmax, L);
+  }
+  std::stable_sort(d.begin(), d.end(), [](const InstDesc& a, const InstDesc& b) { return a.N > b.N; });
+  return LSE_OK;
+}
+
 }  // namespace
+
+cudaStream_t lse_ctx_stream(lse_ctx* c) { return c ? c->stream : nullptr; }
 
 extern "C" {
 
@@ -288,21 +326,12 @@ lse_status lse_fit_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* offset
   if (offsets[0] != 0) return fail(ctx, LSE_EINVAL, "offsets[0] must be 0");
   cudaSetDevice(ctx->cfg.device);
   cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
-  std::vector<InstDesc> d(B);
+  std::vector<InstDesc> d;
   int Nmax = 0, Lmax = 0;
-  for (int b = 0; b < B; ++b) {
-    const int64_t n = offsets[b + 1] - offsets[b];
-    if (n < 2 || n > (1 << 17)) return fail(ctx, LSE_EINVAL, "instance " + std::to_string(b) + ": N out of range");
-    const int N = (int)n;
-    const int L = ctx->cfg.grid_size ? ctx->cfg.grid_size : default_L(N);
-    if (L < 2 * N) return fail(ctx, LSE_EINVAL, "grid size L must be >= 2N");
-    d[b] = InstDesc{offsets[b], N, L, 0, 0, 0, 0};
-    Nmax = std::max(Nmax, N);
-    Lmax = std::max(Lmax, L);
-  }
-  const int prec = ctx->cfg.precision;
-  lse_status s = ensure_tables(ctx, std::max(ilog2((uint32_t)Lmax), ilog2(2u * (uint32_t)Nmax)));
+  lse_status s = plan_fit_descs(ctx, offsets, B, d, Nmax, Lmax);
   if (s) return s;
+  const int prec = ctx->cfg.precision;
+  if ((s = ensure_tables(ctx, std::max(ilog2((uint32_t)Lmax), ilog2(2u * (uint32_t)Nmax))))) return s;
   const int grid = std::min(B, ctx->sm_count);
   const size_t per = fit_workspace_bytes(Nmax, Lmax, prec);
   if ((s = ensure(ctx, ctx->ws, per * grid))) return s;
@@ -332,6 +361,92 @@ lse_status lse_fit_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* offset
     cudaEventDestroy(ev);
   }
   return LSE_OK;
+}
+
+lse_status lse_plan_fit(lse_ctx* ctx, const int64_t* offsets, int32_t B, lse_plan** out) {
+  if (!ctx || !out) return fail(ctx, LSE_EINVAL, "null argument");
+  *out = nullptr;
+  cudaSetDevice(ctx->cfg.device);
+  std::vector<InstDesc> d;
+  int Nmax = 0, Lmax = 0;
+  lse_status s = plan_fit_descs(ctx, offsets, B, d, Nmax, Lmax);
+  if (s) return s;
+  if ((s = ensure_tables(ctx, std::max(ilog2((uint32_t)Lmax), ilog2(2u * (uint32_t)Nmax))))) return s;
+  lse_plan* p = new lse_plan();
+  p->ctx = ctx;
+  p->B = B;
+  p->Nmax = Nmax;
+  p->Lmax = Lmax;
+  p->prec = ctx->cfg.precision;
+  p->grid = std::min(B, ctx->sm_count);
+  if ((s = ensure(ctx, p->desc, d.size() * sizeof(InstDesc))) || (s = ensure(ctx, p->counter, 256)) ||
+      (s = ensure(ctx, p->ws, fit_workspace_bytes(Nmax, Lmax, p->prec) * p->grid))) {
+    lse_plan_destroy(p);
+    return s;
+  }
+  if (cudaMemcpy(p->desc.p, d.data(), d.size() * sizeof(InstDesc), cudaMemcpyHostToDevice) != cudaSuccess) {
+    lse_plan_destroy(p);
+    return fail(ctx, LSE_ECUDA, "descriptor upload failed");
+  }
+  *out = p;
+  return LSE_OK;
+}
+
+lse_status lse_plan_launch(lse_plan* p, const float* y_d, const lse_batch_out* out, void* stream) {
+  if (!p || !y_d || !out) return LSE_EINVAL;
+  lse_ctx* ctx = p->ctx;
+  cudaStream_t st = (cudaStream_t)stream;
+  LSE_CUDA(ctx, cudaMemsetAsync(p->counter.p, 0, sizeof(int), st));
+  const FitConfig fc{ctx->cfg.tau, ctx->cfg.max_outer, ctx->cfg.max_inner, ctx->cfg.approx_activation_iters};
+  const FitOut fo{out->theta, out->gamma, (c128*)out->alpha, out->K, out->beta, out->objective, out->iters,
+                  out->n_evals, out->n_grid, out->status};
+  const cudaError_t e = launch_fit(p->prec, y_d, (const InstDesc*)p->desc.p, p->B, p->Nmax, p->Lmax, fc, tables(ctx),
+                                   fo, p->ws.p, (int*)p->counter.p, p->grid, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "fit kernel launch");
+  return LSE_OK;
+}
+
+lse_status lse_plan_graph_launch(lse_plan* p, const float* y_d, const lse_batch_out* out, void* stream) {
+  if (!p || !y_d || !out) return LSE_EINVAL;
+  lse_ctx* ctx = p->ctx;
+  const bool same = p->exec && p->g_y == y_d && !std::memcmp(&p->g_out, out, sizeof(*out));
+  if (!same) {
+    // capture on the context's own (non-legacy) stream; the graph is launched
+    // on the caller's stream
+    cudaGraph_t g = nullptr;
+    LSE_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    const lse_status s = lse_plan_launch(p, y_d, out, ctx->stream);
+    const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+    if (s) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->exec = nullptr;
+    p->graph = g;
+    LSE_CUDA(ctx, cudaGraphInstantiate(&p->exec, g, 0));
+    p->g_y = y_d;
+    p->g_out = *out;
+  }
+  LSE_CUDA(ctx, cudaGraphLaunch(p->exec, (cudaStream_t)stream));
+  return LSE_OK;
+}
+
+void lse_plan_destroy(lse_plan* p) {
+  if (!p) return;
+  lse_ctx* ctx = p->ctx;
+  cudaSetDevice(ctx->cfg.device);
+  cudaDeviceSynchronize();
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  for (DevBuf* b : {&p->desc, &p->counter, &p->ws})
+    if (b->p) {
+      cudaFree(b->p);
+      ctx->allocated -= b->n;
+    }
+  delete p;
 }
 
 lse_status lse_fit_batch(lse_ctx* ctx, const float* y, const int64_t* offsets, int32_t B, lse_result* outs,
@@ -426,7 +541,7 @@ lse_status lse_eval_grid_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* 
     if (n < 2 || n > (1 << 17) || k < 0 || k > n)
       return fail(ctx, LSE_EINVAL, "instance " + std::to_string(b) + ": N or K out of range");
     if (!is_pow2(L[b]) || L[b] < 2 * n) return fail(ctx, LSE_EINVAL, "L must be a power of two >= 2N");
-    d[b] = InstDesc{y_offsets[b], (int)n, L[b], k_offsets[b], (int)k, 0, g};
+    d[b] = InstDesc{y_offsets[b], (int)n, L[b], k_offsets[b], (int)k, b, g};
     g += L[b];
     Nmax = std::max(Nmax, (int)n);
     Lmax = std::max(Lmax, (int)L[b]);

@@ -616,10 +616,11 @@ struct Fitter {
     }
     __syncthreads();
     FitOut o = A->out;
+    const int ob = d.idx;  // result slot of this instance
     if (yy == 0.0) {  // degenerate: nothing to estimate
       if (threadIdx.x == 0) {
-        o.K[b] = 0; o.beta[b] = 0.0; o.objective[b] = 0.0; o.iters[b] = 0; o.n_evals[b] = 0; o.n_grid[b] = 0;
-        o.status[b] = kST_OK;
+        o.K[ob] = 0; o.beta[ob] = 0.0; o.objective[ob] = 0.0; o.iters[ob] = 0; o.n_evals[ob] = 0; o.n_grid[ob] = 0;
+        o.status[ob] = kST_OK;
       }
       __syncthreads();
       return;
@@ -709,13 +710,13 @@ struct Fitter {
       o.alpha[ro + r] = g * q;
     }
     if (threadIdx.x == 0) {
-      o.K[b] = K;
-      o.beta[b] = sh->beta;
-      o.objective[b] = sh->f_cur - prior_term(K, N, sh->zeta);
-      o.iters[b] = min(it, A->cfg.max_outer);
-      o.n_evals[b] = sh->n_evals;
-      o.n_grid[b] = sh->n_grid;
-      o.status[b] = sh->status != kST_OK ? sh->status : (converged ? kST_OK : kST_NOTCONV);
+      o.K[ob] = K;
+      o.beta[ob] = sh->beta;
+      o.objective[ob] = sh->f_cur - prior_term(K, N, sh->zeta);
+      o.iters[ob] = min(it, A->cfg.max_outer);
+      o.n_evals[ob] = sh->n_evals;
+      o.n_grid[ob] = sh->n_grid;
+      o.status[ob] = sh->status != kST_OK ? sh->status : (converged ? kST_OK : kST_NOTCONV);
     }
     __syncthreads();
   }

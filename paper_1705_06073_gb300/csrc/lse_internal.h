@@ -8,6 +8,10 @@
 
 #include "lse_common.cuh"
 
+struct lse_ctx;
+// the stream a context enqueues on (lse_api.cu)
+cudaStream_t lse_ctx_stream(lse_ctx* c);
+
 namespace lse {
 
 // One instance of a batched launch.
@@ -17,7 +21,7 @@ struct InstDesc {
   int32_t L;       // grid size (power of two >= 2N)
   int64_t k_off;   // eval-grid: offset of this instance's components; fit: unused
   int32_t K;       // eval-grid: number of components
-  int32_t pad;
+  int32_t idx;     // fit: index of the instance's result slots (queue order may differ)
   int64_t g_off;   // eval-grid: offset of this instance's grid outputs
 };
 

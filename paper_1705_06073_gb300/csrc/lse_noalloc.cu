@@ -117,7 +117,7 @@ LSE_API lse_status lse_fit_noalloc_d(const lse_config* cfg, const float* y_d, in
   DeviceSetup* d = nullptr;
   lse_status s = setup(dev, st, &d);
   if (s != LSE_OK) return s;
-  const InstDesc h{0, N, L, 0, 0, 0, 0};
+  const InstDesc h{0, N, L, 0, 0, 0, 0};  // result slot 0
   if (cudaMemcpyAsync(d->desc, &h, sizeof(h), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemsetAsync(d->counter, 0, sizeof(int), st) != cudaSuccess)
     return set_err(LSE_ECUDA, "lse_fit_noalloc_d: staging the launch descriptor failed");

@@ -42,6 +42,13 @@ class lse_result(ctypes.Structure):
                 ("iters", ctypes.c_int32), ("n_evals", ctypes.c_int32), ("n_grid", ctypes.c_int32)]
 
 
+class lse_serve_result(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_int64), ("status", ctypes.c_int32), ("N", ctypes.c_int32),
+                ("K", ctypes.c_int32), ("K_cap", ctypes.c_int32), ("theta", c_double_p), ("gamma", c_double_p),
+                ("alpha", c_double_p), ("beta", ctypes.c_double), ("objective", ctypes.c_double),
+                ("iters", ctypes.c_int32), ("n_evals", ctypes.c_int32)]
+
+
 class lse_batch_out(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_void_p), ("gamma", ctypes.c_void_p), ("alpha", ctypes.c_void_p),
                 ("K", ctypes.c_void_p), ("beta", ctypes.c_void_p), ("objective", ctypes.c_void_p),
@@ -50,7 +57,9 @@ class lse_batch_out(ctypes.Structure):
 
 
 EXPORTS = ["lse_config_default", "lse_create", "lse_destroy", "lse_strerror", "lse_last_error", "lse_fit",
-           "lse_fit_batch", "lse_fit_batch_d", "lse_eval_grid", "lse_eval_grid_batch_d", "lse_kernel_time"]
+           "lse_fit_batch", "lse_fit_batch_d", "lse_eval_grid", "lse_eval_grid_batch_d", "lse_kernel_time",
+           "lse_plan_fit", "lse_plan_launch", "lse_plan_graph_launch", "lse_plan_destroy", "lse_serve_create",
+           "lse_serve_submit", "lse_serve_poll", "lse_serve_in_flight", "lse_serve_device_bytes", "lse_serve_destroy"]
 
 _lib = None
 
@@ -79,6 +88,17 @@ def load(path: str = LIB_PATH):
         "lse_eval_grid_batch_d": (ctypes.c_int, [P, P, c_int64_p, ctypes.c_int32, P, P, c_int64_p, P, c_int32_p,
                                                  ctypes.c_int32, P, P, P, P, P, P, P]),
         "lse_kernel_time": (ctypes.c_int, [P, ctypes.c_int32, c_double_p, c_int64_p]),
+        "lse_plan_fit": (ctypes.c_int, [P, c_int64_p, ctypes.c_int32, ctypes.POINTER(P)]),
+        "lse_plan_launch": (ctypes.c_int, [P, P, ctypes.POINTER(lse_batch_out), P]),
+        "lse_plan_graph_launch": (ctypes.c_int, [P, P, ctypes.POINTER(lse_batch_out), P]),
+        "lse_plan_destroy": (None, [P]),
+        "lse_serve_create": (ctypes.c_int, [ctypes.POINTER(lse_config), ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.POINTER(P)]),
+        "lse_serve_submit": (ctypes.c_int, [P, c_float_p, ctypes.c_int32, ctypes.c_int64]),
+        "lse_serve_poll": (ctypes.c_int32, [P, ctypes.POINTER(lse_serve_result), ctypes.c_int32]),
+        "lse_serve_in_flight": (ctypes.c_int32, [P]),
+        "lse_serve_device_bytes": (ctypes.c_uint64, [P]),
+        "lse_serve_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -193,6 +213,34 @@ def lse_fit_batch_d(ctx, y_d, offsets: np.ndarray, out: dict, stream=None) -> No
     _check(ctx, st)
 
 
+def _batch_out(out: dict):
+    return lse_batch_out(out["theta"].data_ptr(), out["gamma"].data_ptr(), out["alpha"].data_ptr(),
+                         out["K"].data_ptr(), out["beta"].data_ptr(), out["objective"].data_ptr(),
+                         out["iters"].data_ptr(), out["n_evals"].data_ptr(), out["n_grid"].data_ptr(),
+                         out["status"].data_ptr())
+
+
+def lse_plan_fit(ctx, offsets: np.ndarray):
+    """Plan batched fits of the shape `offsets` (host int64 [B+1])."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    h = ctypes.c_void_p()
+    _check(ctx, load().lse_plan_fit(ctx, _ptr(offsets, c_int64_p), len(offsets) - 1, ctypes.byref(h)))
+    return h
+
+
+def lse_plan_launch(plan, y_d, out: dict, stream=None, graph: bool = False) -> None:
+    """Enqueue a planned fit (directly, or as a replay of its CUDA graph)."""
+    bo = _batch_out(out)
+    s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    f = load().lse_plan_graph_launch if graph else load().lse_plan_launch
+    st = f(plan, ctypes.c_void_p(y_d.data_ptr()), ctypes.byref(bo), s)
+    _check(None, st)
+
+
+def lse_plan_destroy(plan) -> None:
+    load().lse_plan_destroy(plan)
+
+
 def alloc_batch_out(offsets: np.ndarray, device="cuda"):
     import torch
     tot = int(offsets[-1])
@@ -271,3 +319,54 @@ def lse_fit_noalloc_d(y_d, N: int, out: dict, cfg: lse_config | None = None, str
     s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
     st = f(ctypes.byref(cfg) if cfg is not None else None, ctypes.c_void_p(y_d.data_ptr()), int(N), ctypes.byref(bo), s)
     _check(None, st)
+
+
+class Server:
+    """Continuous-batching server (lse_serve_*): submit host requests, poll
+    for finished results.  Results are dicts like lse_fit's plus request_id."""
+
+    def __init__(self, cfg: lse_config | None = None, streams: int = 8, max_group: int = 19, K_cap: int = 32768):
+        self.h = ctypes.c_void_p()
+        _check(None, load().lse_serve_create(ctypes.byref(cfg) if cfg is not None else None, streams, max_group,
+                                             ctypes.byref(self.h)))
+        self.K_cap = K_cap
+        self._buf = (lse_serve_result * 64)()
+        self._arr = [(np.zeros(K_cap), np.zeros(K_cap), np.zeros(2 * K_cap)) for _ in range(64)]
+        for i, (th, ga, al) in enumerate(self._arr):
+            self._buf[i].K_cap = K_cap
+            self._buf[i].theta = _ptr(th, c_double_p)
+            self._buf[i].gamma = _ptr(ga, c_double_p)
+            self._buf[i].alpha = _ptr(al, c_double_p)
+
+    def submit(self, y, request_id: int) -> int:
+        y = _c64(y)
+        return load().lse_serve_submit(self.h, y.view(np.float32).ctypes.data_as(c_float_p), y.shape[0],
+                                       int(request_id))
+
+    def poll(self) -> list:
+        out = []
+        while True:
+            n = load().lse_serve_poll(self.h, self._buf, 64)
+            for i in range(n):
+                r = self._buf[i]
+                th, ga, al = self._arr[i]
+                K = r.K
+                ok = r.status != LSE_ECAPACITY
+                out.append(dict(request_id=r.request_id, status=r.status, N=r.N, K=K,
+                                theta=th[:K].copy() if ok else None, gamma=ga[:K].copy() if ok else None,
+                                alpha=(al[0:2 * K:2] + 1j * al[1:2 * K:2]) if ok else None, beta=r.beta,
+                                objective=r.objective, iters=r.iters, n_evals=r.n_evals))
+                self._buf[i].K_cap = self.K_cap
+            if n < 64:
+                return out
+
+    def in_flight(self) -> int:
+        return load().lse_serve_in_flight(self.h)
+
+    def device_bytes(self) -> int:
+        return load().lse_serve_device_bytes(self.h)
+
+    def close(self) -> None:
+        if self.h:
+            load().lse_serve_destroy(self.h)
+            self.h = ctypes.c_void_p()

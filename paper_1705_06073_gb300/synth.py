@@ -104,6 +104,19 @@ class Instance:
         return int(self.y.shape[0])
 
 
+def sum_of_sinusoids(N: int, theta: np.ndarray, alpha: np.ndarray) -> np.ndarray:
+    """h_n = sum_k alpha_k exp(j 2 pi theta_k n), n = 0..N-1.  With n = 64 a + b
+    the phase splits into two small tables, so h is one (N/64 x K)(K x 64)
+    matrix product instead of N K complex exponentials."""
+    if len(theta) == 0:
+        return np.zeros(N, complex)
+    Bn = 64
+    A = (N + Bn - 1) // Bn
+    t1 = np.exp(2j * np.pi * np.outer(theta, np.arange(A, dtype=np.float64) * Bn)) * alpha[:, None]
+    t2 = np.exp(2j * np.pi * np.outer(theta, np.arange(Bn, dtype=np.float64)))
+    return (t1.T @ t2).reshape(-1)[:N]
+
+
 def make_instance(N: int, K: int, snr_db: float, seed: int, *, law: str = "cn",
                   min_sep: float | None = None, noise: bool = True) -> Instance:
     """y = sum_k alpha_k e^{j 2 pi theta_k n} + w, n = 0..N-1 (eq. model, Phi = I).
@@ -114,8 +127,7 @@ def make_instance(N: int, K: int, snr_db: float, seed: int, *, law: str = "cn",
     sep = (2.0 / N) if min_sep is None else min_sep
     theta = draw_frequencies(st, K, sep)
     alpha = draw_amplitudes(st, K, law)
-    n = np.arange(N, dtype=np.float64)
-    h = np.exp(2j * np.pi * np.outer(n, theta)) @ alpha if K else np.zeros(N, complex)
+    h = sum_of_sinusoids(N, theta, alpha)
     beta = float(np.vdot(h, h).real / (N * 10.0 ** (snr_db / 10.0))) if K else 1.0
     w = math.sqrt(beta) * st.cnormal(N) if noise else 0.0
     y = (h + w).astype(np.complex64)
