@@ -235,4 +235,89 @@ __device__ LevResult block_levinson_df(c128* c64, c128* a64, int N, float4* red,
   return r;
 }
 
+// ---------------------------------------------------------------------------
+// Off-grid sums of block_active_sums (R_0..R_3 from rho, X_0..X_2 from x with
+// the centred weights (n - c)^a, phases e^{-j2pi n theta_k}) in double-float
+// on the FP32 pipes.  rho_df, x_df: the FP64 vectors converted once per
+// evaluation (float4 {re.h, re.l, im.h, im.l}).  One warp per component;
+// lane l visits n = l + 32 j with the phase advanced by e^{-j2pi 32 theta}
+// and restarted every 64 steps from e^{-j2pi l theta} (e^{-j2pi 2048 theta})^i,
+// all three phase factors formed once per component in FP64.  Output in FP64,
+// same layout as block_active_sums.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cmul_df(f2 ar, f2 ai, f2 br, f2 bi, f2& cr, f2& ci) {
+  cr = axpy2(f2{0.f, 0.f}, ar, br, neg(ai), bi);
+  ci = axpy2(f2{0.f, 0.f}, ar, bi, ai, br);
+}
+
+template <int NT>
+__device__ void block_active_sums_df(const float4* rho_df, const float4* x_df, const double* theta, int K, int N,
+                                     c128* sums) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float cen = 0.5f * (float)(N - 2);  // exact: N < 2^24
+  for (int k = warp; k < K; k += NT / 32) {
+    const double th = theta[k];
+    const c128 st64 = unit_phase(32.0, th, -1.0);
+    const c128 big64 = unit_phase(2048.0, th, -1.0);
+    const c128 e064 = unit_phase((double)lane, th, -1.0);
+    const f2 sr = to_f2(st64.re), si = to_f2(st64.im);
+    const f2 br = to_f2(big64.re), bi = to_f2(big64.im);
+    f2 ar = to_f2(e064.re), ai = to_f2(e064.im);  // anchor e^{-j2pi (l + 2048 i) theta}
+    f2 er = ar, ei = ai;
+    float S[14], E[14];
+#pragma unroll
+    for (int j = 0; j < 14; ++j) { S[j] = 0.f; E[j] = 0.f; }
+    int it = 0;
+    for (int n = lane; n < N; n += 32, ++it) {
+      if (it && (it & 63) == 0) {  // next anchor
+        f2 nr, ni;
+        cmul_df(ar, ai, br, bi, nr, ni);
+        ar = nr; ai = ni;
+        er = ar; ei = ai;
+      }
+      const float4 rv = rho_df[n], xv = x_df[n];
+      f2 pr, pi, qr, qi;
+      cmul_df(re_of(rv), im_of(rv), er, ei, pr, pi);  // rho_n e
+      cmul_df(re_of(xv), im_of(xv), er, ei, qr, qi);  // x_n e
+      const f2 w1{(float)n - cen, 0.f};               // exact (half-integer at worst)
+      float w2h, w2l;
+      w2h = __fmul_rn(w1.h, w1.h);
+      w2l = __fmaf_rn(w1.h, w1.h, -w2h);
+      const f2 w2{w2h, w2l};
+      const f2 w3 = mul(w2, w1);
+      acc_merge(S[0], E[0], pr.h, pr.l);
+      acc_merge(S[1], E[1], pi.h, pi.l);
+      acc_prod(S[2], E[2], pr, w1);
+      acc_prod(S[3], E[3], pi, w1);
+      acc_prod(S[4], E[4], pr, w2);
+      acc_prod(S[5], E[5], pi, w2);
+      acc_prod(S[6], E[6], pr, w3);
+      acc_prod(S[7], E[7], pi, w3);
+      acc_merge(S[8], E[8], qr.h, qr.l);
+      acc_merge(S[9], E[9], qi.h, qi.l);
+      acc_prod(S[10], E[10], qr, w1);
+      acc_prod(S[11], E[11], qi, w1);
+      acc_prod(S[12], E[12], qr, w2);
+      acc_prod(S[13], E[13], qi, w2);
+      f2 nr, ni;
+      cmul_df(er, ei, sr, si, nr, ni);
+      er = nr; ei = ni;
+    }
+#pragma unroll
+    for (int j = 0; j < 14; ++j) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, S[j], o), e2 = __shfl_xor_sync(0xffffffffu, E[j], o);
+        acc_merge(S[j], E[j], s2, e2);
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int j = 0; j < 7; ++j)
+        sums[k * 7 + j] = mk((double)S[2 * j] + (double)E[2 * j], (double)S[2 * j + 1] + (double)E[2 * j + 1]);
+    }
+  }
+  __syncthreads();
+}
+
 }  // namespace lse

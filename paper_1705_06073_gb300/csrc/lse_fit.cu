@@ -70,6 +70,7 @@ struct Work {
   cx<TG>* gbuf[4];  // grid FFT buffers, Lmax each
   double *theta, *gamma, *th_t, *ga_t, *dth, *dga;
   c128* sums;       // 7 * Nmax off-grid sums (FP64 on every path)
+  float4 *rho_df, *x_df;  // Nmax each: rho and x as double-float pairs (double-float path)
   double* dl;       // Lmax
   int* cand;        // Lmax
   double *cand_dl, *cand_s;  // Lmax: decision values of the candidates
@@ -98,6 +99,8 @@ __host__ __device__ inline Layout make_layout(int Nmax, int Lmax) {
   for (int j = 0; j < 4; ++j) put(sizeof(cx<TG>) * (size_t)Lmax);      // gbuf
   for (int j = 0; j < 6; ++j) put(sizeof(double) * (size_t)Nmax);      // theta..dga
   put(sizeof(c128) * 7 * (size_t)Nmax);                                 // sums
+  put(sizeof(float4) * (size_t)Nmax);                                   // rho_df
+  put(sizeof(float4) * (size_t)Nmax);                                   // x_df
   put(sizeof(double) * (size_t)Lmax);                                   // dl
   put(sizeof(int) * (size_t)Lmax);                                      // cand
   put(sizeof(double) * (size_t)Lmax);                                   // cand_dl
@@ -130,6 +133,8 @@ __device__ Work<TG> carve(char* base, int Nmax, int Lmax) {
   w.dth = (double*)(base + L.off[i++]);
   w.dga = (double*)(base + L.off[i++]);
   w.sums = (c128*)(base + L.off[i++]);
+  w.rho_df = (float4*)(base + L.off[i++]);
+  w.x_df = (float4*)(base + L.off[i++]);
   w.dl = (double*)(base + L.off[i++]);
   w.cand = (int*)(base + L.off[i++]);
   w.cand_dl = (double*)(base + L.off[i++]);
@@ -213,15 +218,26 @@ struct Fitter {
       sh->f_cur = lr.logdet + yCy;
     }
     __syncthreads();
+    if constexpr (PREC == 2) {  // double-float copies for the sums
+      for (int n = threadIdx.x; n < N; n += kNT) {
+        const c128 r = w.rho[n], v = w.x[n];
+        w.rho_df[n] = pack(to_f2(r.re), to_f2(r.im));
+        w.x_df[n] = pack(to_f2(v.re), to_f2(v.im));
+      }
+      __syncthreads();
+    }
     if (want_sums && K > 0) compute_sums(th, K);
     return 0;
   }
 
-  // The Newton sums stay FP64 on every path: in FP32 the gradient terms
+  // The Newton sums keep FP64 accuracy on every path (FP64, or double-float
+  // on the FP32 pipes for the double-float path): in FP32 the gradient terms
   // (e.g. s - |q|^2 near convergence) cancel catastrophically, the Newton
   // directions disagree with the FP64 objective and the line search stalls.
   __device__ void compute_sums(const double* th, int K) {
-    if (K > 0) block_active_sums<kNT, double>(w.rho, w.x, th, K, N, w.sums);
+    if (K <= 0) return;
+    if constexpr (PREC == 2) block_active_sums_df<kNT>(w.rho_df, w.x_df, th, K, N, w.sums);
+    else block_active_sums<kNT, double>(w.rho, w.x, th, K, N, w.sums);
   }
 
   // ---------------------------------------------------------------- grid ---
@@ -282,7 +298,8 @@ struct Fitter {
   __device__ void rescore(const int* ls, int n, double* dl_out, double* s_out, c128* q_out, int K) {
     for (int j = threadIdx.x; j < n; j += kNT) w.rs_theta[j] = (double)ls[j] / (double)L;
     __syncthreads();
-    block_active_sums<kNT, double>(w.rho, w.x, w.rs_theta, n, N, w.rs_sums);
+    if constexpr (PREC == 2) block_active_sums_df<kNT>(w.rho_df, w.x_df, w.rs_theta, n, N, w.rs_sums);
+    else block_active_sums<kNT, double>(w.rho, w.x, w.rs_theta, n, N, w.rs_sums);
     const double inv_delta = 1.0 / sh->delta_last;
     for (int j = threadIdx.x; j < n; j += kNT) {
       const c128* sm = w.rs_sums + 7 * j;
