@@ -85,6 +85,13 @@ __device__ __forceinline__ f2 sub(f2 x, f2 y) {
   const f2 s = two_sum(x.h, -y.h);
   return two_sum(s.h, __fadd_rn(__fsub_rn(x.l, y.l), s.l));
 }
+// 1 / y (one Newton correction after the FP32 reciprocal)
+__device__ __forceinline__ f2 recip(f2 y) {
+  const float r = __fdiv_rn(1.f, y.h);
+  const f2 e = sub(f2{1.f, 0.f}, mul(y, f2{r, 0.f}));
+  return two_sum(r, __fmul_rn(r, e.h));
+}
+
 // x / y (one correction step after the FP32 quotient)
 __device__ __forceinline__ f2 div(f2 x, f2 y) {
   const float q1 = __fdiv_rn(x.h, y.h);
@@ -136,6 +143,16 @@ __device__ LevResult block_levinson_df(c128* c64, c128* a64, int N, float4* red,
   int bad = !(c0 > 0.0 && isfinite(c0));
   for (int n = 1; n < N && !bad; ++n) {
     const bool more = (n + 1) < N;
+    // pivot of this order, delta_n = delta_{n-1} (1 - |k_n|^2), and its
+    // reciprocal: they need only k_n, so they are issued before the pair loop
+    // and their latency hides behind it
+    float p1, q1, p2, q2;
+    prod_terms(kr, kr, p1, q1);
+    prod_terms(ki, ki, p2, q2);
+    const f2 k2a = two_sum(p1, p2);
+    const f2 k2 = two_sum(k2a.h, __fadd_rn(__fadd_rn(q1, q2), k2a.l));
+    const f2 dn = mul(delta, sub(f2{1.f, 0.f}, k2));
+    const f2 inv_dn = recip(dn);
     float S0 = 0.f, E0 = 0.f, S1 = 0.f, E1 = 0.f, S2 = 0.f, E2 = 0.f, S3 = 0.f, E3 = 0.f;
     for (int i = threadIdx.x; 2 * i <= n; i += NT) {
       const int j = n - i;
@@ -196,13 +213,6 @@ __device__ LevResult block_levinson_df(c128* c64, c128* a64, int N, float4* red,
     e0 = __shfl_sync(0xffffffffu, e0, 0);
     s1 = __shfl_sync(0xffffffffu, s1, 0);
     e1 = __shfl_sync(0xffffffffu, e1, 0);
-    // delta_n = delta_{n-1} (1 - |k_n|^2)
-    float p1, q1, p2, q2;
-    prod_terms(kr, kr, p1, q1);
-    prod_terms(ki, ki, p2, q2);
-    const f2 k2a = two_sum(p1, p2);
-    const f2 k2 = two_sum(k2a.h, __fadd_rn(__fadd_rn(q1, q2), k2a.l));
-    const f2 dn = mul(delta, sub(f2{1.f, 0.f}, k2));
     if (!(dn.h > 0.f) || !isfinite(dn.h) || !isfinite(s0) || !isfinite(s1)) {
       bad = 1;
       break;
@@ -216,8 +226,8 @@ __device__ LevResult block_levinson_df(c128* c64, c128* a64, int N, float4* red,
     expo += ex;
     if (more) {
       const f2 er = two_sum(s0, e0), ei = two_sum(s1, e1);
-      kr = neg(div(er, dn));
-      ki = neg(div(ei, dn));
+      kr = neg(mul(er, inv_dn));
+      ki = neg(mul(ei, inv_dn));
     }
   }
   LevResult r;

@@ -27,7 +27,7 @@ namespace {
 
 constexpr int kFNT = 256;
 template <bool DF>
-__host__ __device__ constexpr int factor_threads() { return DF ? 512 : 256; }
+__host__ __device__ constexpr int factor_threads() { return 256; }
 
 struct FactorLayout {
   size_t y, c, a, Yf, buf, total, M2;
