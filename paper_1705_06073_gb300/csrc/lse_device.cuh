@@ -151,6 +151,7 @@ struct LevShared {
   float4 kdf;    // the same as a double-float pair (double-float recursion)
   double delta;  // current pivot
   double mant;   // ln|C| accumulated as mant * 2^expo
+  double logdet; // ln|C| (double-float recursion: result for the whole block)
   int expo;
   int status;    // 0 ok, 1 non-positive / non-finite pivot
 };

@@ -100,25 +100,89 @@ __device__ __forceinline__ f2 div(f2 x, f2 y) {
   return two_sum(q1, q2);
 }
 
+// a + b when |a| >= |b| (or a = 0): Dekker's Fast2Sum, exact under that
+// condition (used only to renormalise a head and its small correction)
+__device__ __forceinline__ f2 fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return f2{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// x + y1*z1 + y2*z2 with the final renormalisation by Fast2Sum
+__device__ __forceinline__ f2 axpy2f(f2 x, f2 y1, f2 z1, f2 y2, f2 z2) {
+  float p1, e1, p2, e2;
+  prod_terms(y1, z1, p1, e1);
+  prod_terms(y2, z2, p2, e2);
+  const f2 s = two_sum(x.h, p1);
+  const f2 t = two_sum(s.h, p2);
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(x.l, e1), __fadd_rn(e2, s.l)), t.l);
+  return fast_two_sum(t.h, lo);
+}
+
+// the four running sums of one thread's share of e = sum_i a_i c_{n+1-i}:
+// Re a Re c, -Im a Im c, Re a Im c, Im a Re c (each S + E)
+struct LevAcc {
+  float S0, E0, S1, E1, S2, E2, S3, E3;
+};
+
+__device__ __forceinline__ void lev_acc(LevAcc& A, f2 r, f2 i, float4 c4) {
+  const f2 cr = re_of(c4), ci = im_of(c4);
+  acc_prod(A.S0, A.E0, r, cr);
+  acc_prod(A.S1, A.E1, neg(i), ci);
+  acc_prod(A.S2, A.E2, r, ci);
+  acc_prod(A.S3, A.E3, i, cr);
+}
+
+// One pair (i, j = n - i) of an order: a_i + k conj(a_j) and a_j + k conj(a_i)
+// from the loaded old values, stored where st_i / st_j, and both new values'
+// products with their column entries (ci4 for entry i, cj4 for entry j; a
+// zero entry adds exactly nothing) accumulated into A.
+__device__ __forceinline__ void lev_pair(float4* a, float4 ai, float4 aj, f2 kr, f2 ki, int i, int j, bool st_i,
+                                         bool st_j, float4 ci4, float4 cj4, LevAcc& A) {
+  const f2 air = re_of(ai), aii = im_of(ai), ajr = re_of(aj), aji = im_of(aj);
+  const f2 nir = axpy2f(air, kr, ajr, ki, aji);
+  const f2 nii = axpy2f(aii, ki, ajr, neg(kr), aji);
+  const f2 njr = axpy2f(ajr, kr, air, ki, aii);
+  const f2 nji = axpy2f(aji, ki, air, neg(kr), aii);
+  if (st_i) a[i] = pack(nir, nii);
+  if (st_j) a[j] = pack(njr, nji);
+  lev_acc(A, nir, nii, ci4);
+  lev_acc(A, njr, nji, cj4);
+}
+
+// barrier over the first NTL threads of the block (named barrier 1)
+template <int NTL>
+__device__ __forceinline__ void lev_bar() {
+  asm volatile("bar.sync 1, %0;" ::"n"(NTL) : "memory");
+}
+
 // ---------------------------------------------------------------------------
-// The Levinson-Durbin recursion of block_levinson (same orders, same fused
-// update + next inner product per pair (i, n-i)), with the vectors, the
-// reflection coefficient, the pivot and the running product of pivots all in
-// double-float on the FP32 pipes.  The first column is scaled by 1/c_0 so that
-// every value stays near unit magnitude; pivots and ln|C| are returned in the
-// unscaled units.
+// The Levinson-Durbin recursion of block_levinson (same orders, same update of
+// every pair (i, n-i) fused with the next inner product), with the vectors,
+// the reflection coefficient, the pivot and the running product of pivots all
+// in double-float on the FP32 pipes.  The first column is scaled by 1/c_0 so
+// that every value stays near unit magnitude; pivots and ln|C| are returned in
+// the unscaled units.
 //
-// One barrier per order: every warp writes its partial inner product into a
-// double-buffered slot, and after the barrier every warp reduces all slots and
-// forms the next reflection coefficient itself (the same operations on the
-// same data, so all warps agree exactly).  The inner product is split over
-// four accumulators per thread to shorten dependency chains.
+// Only the first NTL = 128 threads (one warp per SM sub-partition) run the
+// orders; the rest of the block waits at the closing barrier.  Every order
+// ends with each warp's partial inner product in a double-buffered shared slot
+// and one barrier among those threads; then every thread sums the NTL/32 slots
+// in the same fixed tree and forms the next reflection coefficient itself, so
+// all of them hold bit-identical scalars.  The redundant per-order scalar work
+// is paid per warp, which is why fewer, busier warps win: at N = 4096 four
+// warps ran the recursion about 13% faster than eight.
+// Each thread takes two pairs per step without branches (a missing pair reads
+// c[0], stores nothing and accumulates zeros), and the pivot of the order,
+// which needs only k_n, is formed in the same straight-line block as the first
+// two pairs so that its dependency chain overlaps their arithmetic.
 // c: FP64 first column, converted in place to double-float (same 16 bytes per
-// element); a: output predictor in FP64.  red: 2*NT/32 float4 of shared memory.
+// element); a: output predictor in FP64.  red: 2*NTL/32 float4 of shared
+// memory; sh: receives the results for the threads that did not take part.
 // ---------------------------------------------------------------------------
-template <int NT>
+template <int NT, int NTL = 128>
 __device__ LevResult block_levinson_df(c128* c64, c128* a64, int N, float4* red, LevShared* sh) {
-  constexpr int NW = NT / 32;
+  static_assert(NTL % 32 == 0 && NTL <= NT, "recursion threads");
+  constexpr int NW = NTL / 32;
   float4* c = reinterpret_cast<float4*>(c64);
   float4* a = reinterpret_cast<float4*>(a64);
   const double c0 = c64[0].re;
@@ -130,118 +194,117 @@ __device__ LevResult block_levinson_df(c128* c64, c128* a64, int N, float4* red,
     a[i] = make_float4(i == 0 ? 1.f : 0.f, 0.f, 0.f, 0.f);
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // per-thread copies of the scalar state (identical in every thread)
-  f2 kr{0.f, 0.f}, ki{0.f, 0.f};
-  if (N > 1) {
-    const float4 c1 = c[1];
-    kr = neg(re_of(c1));
-    ki = neg(im_of(c1));
-  }
-  f2 delta{1.f, 0.f}, mant{1.f, 0.f};
-  int expo = 0;
-  int bad = !(c0 > 0.0 && isfinite(c0));
-  for (int n = 1; n < N && !bad; ++n) {
-    const bool more = (n + 1) < N;
-    // pivot of this order, delta_n = delta_{n-1} (1 - |k_n|^2), and its
-    // reciprocal: they need only k_n, so they are issued before the pair loop
-    // and their latency hides behind it
-    float p1, q1, p2, q2;
-    prod_terms(kr, kr, p1, q1);
-    prod_terms(ki, ki, p2, q2);
-    const f2 k2a = two_sum(p1, p2);
-    const f2 k2 = two_sum(k2a.h, __fadd_rn(__fadd_rn(q1, q2), k2a.l));
-    const f2 dn = mul(delta, sub(f2{1.f, 0.f}, k2));
-    const f2 inv_dn = recip(dn);
-    float S0 = 0.f, E0 = 0.f, S1 = 0.f, E1 = 0.f, S2 = 0.f, E2 = 0.f, S3 = 0.f, E3 = 0.f;
-    for (int i = threadIdx.x; 2 * i <= n; i += NT) {
-      const int j = n - i;
-      const float4 ai = a[i], aj = a[j];
-      const f2 air = re_of(ai), aii = im_of(ai), ajr = re_of(aj), aji = im_of(aj);
-      // a_i + k conj(a_j)
-      const f2 nir = axpy2(air, kr, ajr, ki, aji);
-      const f2 nii = axpy2(aii, ki, ajr, neg(kr), aji);
-      a[i] = pack(nir, nii);
-      if (more) {
-        const float4 cc = c[n + 1 - i];
-        const f2 cr = re_of(cc), ci = im_of(cc);
-        acc_prod(S0, E0, nir, cr);
-        acc_prod(S1, E1, neg(nii), ci);
-        acc_prod(S2, E2, nir, ci);
-        acc_prod(S3, E3, nii, cr);
+  if (threadIdx.x < NTL) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    f2 kr{0.f, 0.f}, ki{0.f, 0.f};
+    if (N > 1) {
+      const float4 c1 = c[1];
+      kr = neg(re_of(c1));
+      ki = neg(im_of(c1));
+    }
+    f2 delta{1.f, 0.f}, mant{1.f, 0.f};
+    int expo = 0;
+    int bad = !(c0 > 0.0 && isfinite(c0));
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int n = 1; n < N && !bad; ++n) {
+      const bool more = (n + 1) < N;
+      LevAcc A{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      f2 dn, inv_dn;
+      {
+        const int i0 = threadIdx.x, i1 = threadIdx.x + NTL;
+        const bool v0 = 2 * i0 <= n, v1 = 2 * i1 <= n;
+        const int ia = v0 ? i0 : 0, ib = v1 ? i1 : 0;
+        const int ja = v0 ? n - ia : 0, jb = v1 ? n - ib : 0;
+        const float4* pa = v0 ? a : c;
+        const float4* pb = v1 ? a : c;
+        const float4 aa_i = pa[ia], aa_j = pa[ja], ab_i = pb[ib], ab_j = pb[jb];
+        const bool wa_i = v0 && more, wa_j = wa_i && ja != ia, wb_i = v1 && more, wb_j = wb_i && jb != ib;
+        const float4 ca_i = c[wa_i ? n + 1 - ia : 0], ca_j = c[wa_j ? ia + 1 : 0];
+        const float4 cb_i = c[wb_i ? n + 1 - ib : 0], cb_j = c[wb_j ? ib + 1 : 0];
+        // pivot of this order, delta_n = delta_{n-1} (1 - |k_n|^2), and 1/delta_n
+        float p1, q1, p2, q2;
+        prod_terms(kr, kr, p1, q1);
+        prod_terms(ki, ki, p2, q2);
+        const f2 k2a = two_sum(p1, p2);
+        const f2 k2 = two_sum(k2a.h, __fadd_rn(__fadd_rn(q1, q2), k2a.l));
+        dn = mul(delta, sub(f2{1.f, 0.f}, k2));
+        inv_dn = recip(dn);
+        lev_pair(a, aa_i, aa_j, kr, ki, ia, ja, v0, v0 && ja != ia, wa_i ? ca_i : z4, wa_j ? ca_j : z4, A);
+        lev_pair(a, ab_i, ab_j, kr, ki, ib, jb, v1, v1 && jb != ib, wb_i ? cb_i : z4, wb_j ? cb_j : z4, A);
       }
-      if (j != i) {
-        const f2 njr = axpy2(ajr, kr, air, ki, aii);
-        const f2 nji = axpy2(aji, ki, air, neg(kr), aii);
-        a[j] = pack(njr, nji);
-        if (more) {
-          const float4 cc = c[i + 1];
-          const f2 cr = re_of(cc), ci = im_of(cc);
-          acc_prod(S0, E0, njr, cr);
-          acc_prod(S1, E1, neg(nji), ci);
-          acc_prod(S2, E2, njr, ci);
-          acc_prod(S3, E3, nji, cr);
+      for (int ia = threadIdx.x + 2 * NTL; 2 * ia <= n; ia += 2 * NTL) {
+        const int i1 = ia + NTL;
+        const bool v1 = 2 * i1 <= n;
+        const int ib = v1 ? i1 : 0;
+        const int ja = n - ia, jb = v1 ? n - ib : 0;
+        const float4* pb = v1 ? a : c;
+        const float4 aa_i = a[ia], aa_j = a[ja], ab_i = pb[ib], ab_j = pb[jb];
+        const bool wa_j = more && ja != ia, wb_i = v1 && more, wb_j = wb_i && jb != ib;
+        const float4 ca_i = c[more ? n + 1 - ia : 0], ca_j = c[wa_j ? ia + 1 : 0];
+        const float4 cb_i = c[wb_i ? n + 1 - ib : 0], cb_j = c[wb_j ? ib + 1 : 0];
+        lev_pair(a, aa_i, aa_j, kr, ki, ia, ja, true, ja != ia, more ? ca_i : z4, wa_j ? ca_j : z4, A);
+        lev_pair(a, ab_i, ab_j, kr, ki, ib, jb, v1, v1 && jb != ib, wb_i ? cb_i : z4, wb_j ? cb_j : z4, A);
+      }
+      acc_merge(A.S0, A.E0, A.S1, A.E1);
+      acc_merge(A.S2, A.E2, A.S3, A.E3);
+      float S0 = A.S0, E0 = A.E0, S2 = A.S2, E2 = A.E2;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float sr = __shfl_xor_sync(0xffffffffu, S0, o), er = __shfl_xor_sync(0xffffffffu, E0, o);
+        const float si = __shfl_xor_sync(0xffffffffu, S2, o), ei = __shfl_xor_sync(0xffffffffu, E2, o);
+        acc_merge(S0, E0, sr, er);
+        acc_merge(S2, E2, si, ei);
+      }
+      float4* slot = red + (n & 1) * NW;
+      if (lane == 0) slot[warp] = make_float4(S0, E0, S2, E2);
+      lev_bar<NTL>();
+      // the same fixed tree over the slots in every thread
+      float4 v[NW];
+#pragma unroll
+      for (int w = 0; w < NW; ++w) v[w] = slot[w];
+#pragma unroll
+      for (int st = 1; st < NW; st <<= 1) {
+#pragma unroll
+        for (int w = 0; w < NW; w += 2 * st) {
+          acc_merge(v[w].x, v[w].y, v[w + st].x, v[w + st].y);
+          acc_merge(v[w].z, v[w].w, v[w + st].z, v[w + st].w);
         }
       }
+      const float s0 = v[0].x, e0 = v[0].y, s1 = v[0].z, e1 = v[0].w;
+      if (!(dn.h > 0.f) || !isfinite(dn.h) || !isfinite(s0) || !isfinite(s1)) {
+        bad = 1;
+        break;
+      }
+      delta = dn;
+      // running product of the pivots, kept in [0.5, 1) with a separate exponent
+      const f2 m = mul(mant, dn);
+      int ex;
+      const float mh = frexpf(m.h, &ex);
+      mant = f2{mh, ldexpf(m.l, -ex)};
+      expo += ex;
+      if (more) {
+        const f2 er = two_sum(s0, e0), ei = two_sum(s1, e1);
+        kr = neg(mul(er, inv_dn));
+        ki = neg(mul(ei, inv_dn));
+      }
     }
-    acc_merge(S0, E0, S1, E1);
-    acc_merge(S2, E2, S3, E3);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float sr = __shfl_xor_sync(0xffffffffu, S0, o), er = __shfl_xor_sync(0xffffffffu, E0, o);
-      const float si = __shfl_xor_sync(0xffffffffu, S2, o), ei = __shfl_xor_sync(0xffffffffu, E2, o);
-      acc_merge(S0, E0, sr, er);
-      acc_merge(S2, E2, si, ei);
-    }
-    float4* slot = red + (n & 1) * NW;
-    if (lane == 0) slot[warp] = make_float4(S0, E0, S2, E2);
-    __syncthreads();
-    // every warp: total of all partials (butterfly: all lanes end with it)
-    const float4 v = lane < NW ? slot[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float s0 = v.x, e0 = v.y, s1 = v.z, e1 = v.w;
-#pragma unroll
-    for (int o = NW / 2; o > 0; o >>= 1) {
-      const float a0 = __shfl_xor_sync(0xffffffffu, s0, o), b0 = __shfl_xor_sync(0xffffffffu, e0, o);
-      const float a1 = __shfl_xor_sync(0xffffffffu, s1, o), b1 = __shfl_xor_sync(0xffffffffu, e1, o);
-      acc_merge(s0, e0, a0, b0);
-      acc_merge(s1, e1, a1, b1);
-    }
-    // lanes < NW now hold the total; give every lane lane 0's copy so that all
-    // threads of the block continue from bit-identical scalars (the loop exit
-    // below must be block-uniform)
-    s0 = __shfl_sync(0xffffffffu, s0, 0);
-    e0 = __shfl_sync(0xffffffffu, e0, 0);
-    s1 = __shfl_sync(0xffffffffu, s1, 0);
-    e1 = __shfl_sync(0xffffffffu, e1, 0);
-    if (!(dn.h > 0.f) || !isfinite(dn.h) || !isfinite(s0) || !isfinite(s1)) {
-      bad = 1;
-      break;
-    }
-    delta = dn;
-    // running product of the pivots, kept in [0.5, 1) with a separate exponent
-    const f2 m = mul(mant, dn);
-    int ex;
-    const float mh = frexpf(m.h, &ex);
-    mant = f2{mh, ldexpf(m.l, -ex)};
-    expo += ex;
-    if (more) {
-      const f2 er = two_sum(s0, e0), ei = two_sum(s1, e1);
-      kr = neg(mul(er, inv_dn));
-      ki = neg(mul(ei, inv_dn));
+    if (threadIdx.x == 0) {
+      sh->status = bad;
+      sh->delta = to_d(delta) * c0;
+      sh->logdet = log(to_d(mant)) + expo * 0.69314718055994530942 + (double)N * log(c0);
     }
   }
-  LevResult r;
-  r.status = bad;
-  r.delta_last = to_d(delta) * c0;
-  r.logdet = log(to_d(mant)) + expo * 0.69314718055994530942 + (double)N * log(c0);
   __syncthreads();
+  LevResult r;
+  r.status = sh->status;
+  r.delta_last = sh->delta;
+  r.logdet = sh->logdet;
   // back to FP64 in place
   for (int i = threadIdx.x; i < N; i += NT) {
     const float4 v = a[i];
     a64[i] = mk(to_d(re_of(v)), to_d(im_of(v)));
   }
   __syncthreads();
-  (void)sh;
   return r;
 }
 
