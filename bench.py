@@ -46,10 +46,39 @@ def levinson_flops(n: int) -> float:
 
 def levinson_df_flops(n: int) -> float:
     """FP32 flops of one double-float Levinson factorisation as implemented:
-    per pair (i, n-i) of an order, four double-float axpy2 updates (36 flops:
-    two TwoProd-with-cross-terms of 7, three TwoSum of 6, four adds) and eight
-    product accumulations (15 flops) = 264 flops; about n^2/4 pairs in all."""
-    return 264.0 * n * n / 4.0
+    per pair (i, n-i) of an order, four double-float updates x + y1 z1 + y2 z2
+    (33 flops: two TwoProd-with-cross-terms of 7, two TwoSum of 6, four adds,
+    one Fast2Sum of 3) and eight product accumulations (15 flops) = 252 flops;
+    about n^2/4 pairs in all."""
+    return 252.0 * n * n / 4.0
+
+
+# DRAM traffic of fit_kernel<2> (dram__bytes_read.sum + dram__bytes_write.sum,
+# one ncu capture of the 8-instance case of this workload, divided by 8) and
+# the digest of the CUDA sources it was taken on; reported only while the
+# sources are unchanged.
+FIT_TRAFFIC = {"sources_sha256": "4b9279347d8543dc5418f7b24a8b92a69770efaaed38ff1d47788fbca362877c",
+               "bytes_per_instance": (3732736 + 1217792) / 8}
+
+
+def sources_digest() -> str:
+    """sha256 over the CUDA sources and the public header, in name order."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1705_06073_gb300", "csrc")
+    files = sorted(os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith((".cu", ".cuh", ".h")))
+    files.append(os.path.join(ROOT, "include", "lse.h"))
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def fit_traffic(b: int):
+    if FIT_TRAFFIC["bytes_per_instance"] is None or FIT_TRAFFIC["sources_sha256"] != sources_digest():
+        return None
+    return FIT_TRAFFIC["bytes_per_instance"] * b
 
 
 def grid_bytes(n: int, l: int, f64: bool) -> float:
@@ -484,10 +513,10 @@ def main():
         "gpu_launches": int(m["launches"]),
         "e2e": {"value": e2e_val, "unit": "fitted instances/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                     "kernel": "fit_kernel<2> (double-float Levinson recursion dominates)",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": fit_traffic(Bn),
+                     "kernel": "fit_kernel<2> (double-float Levinson recursion dominates; clusters of two blocks when 2B <= 152)",
                      "peak_source": "FP32 pipe: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived)",
-                     "sms_busy": min(Bn, 152)},
+                     "sms_busy": 2 * Bn if 2 * Bn <= 152 else min(Bn, 152)},
         "fit": {"iters_mean": None, "n_evals_mean": float(np.mean(m["n_evals"])),
                 "n_grid_mean": float(np.mean(m["n_grid"])), "K_mean": float(np.mean(m["K"])),
                 "status_nonzero": int(np.count_nonzero(m["status"])), "fit_kernel_ms": m["kernel_ms"]},

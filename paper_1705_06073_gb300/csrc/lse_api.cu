@@ -262,7 +262,7 @@ lse_status lse_create(const lse_config* cfg, lse_ctx** out) {
   if (c.precision != LSE_PREC_FP64 && c.precision != LSE_PREC_MIXED && c.precision != LSE_PREC_MIXED_DF)
     return LSE_EINVAL;
   if (c.max_outer < 1 || c.max_inner < 0 || c.approx_activation_iters < 0 || !(c.tau >= 0.0) ||
-      (c.flags & ~(uint64_t)LSE_FLAG_NO_AUTOTUNE))
+      (c.flags & ~(uint64_t)(LSE_FLAG_NO_AUTOTUNE | LSE_FLAG_NO_CLUSTER)))
     return LSE_EINVAL;
   if (c.grid_size < 0 || (c.grid_size > 0 && !is_pow2(c.grid_size))) return LSE_EINVAL;
   int ndev = 0;
@@ -344,7 +344,8 @@ lse_status lse_fit_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* offset
     cudaEventDestroy(e);
   }
   LSE_CUDA(ctx, cudaMemsetAsync(ctx->counter.p, 0, sizeof(int), st));
-  FitConfig fc{ctx->cfg.tau, ctx->cfg.max_outer, ctx->cfg.max_inner, ctx->cfg.approx_activation_iters};
+  FitConfig fc{ctx->cfg.tau, ctx->cfg.max_outer, ctx->cfg.max_inner, ctx->cfg.approx_activation_iters,
+               !(ctx->cfg.flags & LSE_FLAG_NO_CLUSTER)};
   FitOut fo{out->theta, out->gamma, (c128*)out->alpha, out->K, out->beta, out->objective, out->iters,
             out->n_evals, out->n_grid, out->status};
   record(ctx, 0, st, true);
@@ -397,7 +398,8 @@ lse_status lse_plan_launch(lse_plan* p, const float* y_d, const lse_batch_out* o
   lse_ctx* ctx = p->ctx;
   cudaStream_t st = (cudaStream_t)stream;
   LSE_CUDA(ctx, cudaMemsetAsync(p->counter.p, 0, sizeof(int), st));
-  const FitConfig fc{ctx->cfg.tau, ctx->cfg.max_outer, ctx->cfg.max_inner, ctx->cfg.approx_activation_iters};
+  const FitConfig fc{ctx->cfg.tau, ctx->cfg.max_outer, ctx->cfg.max_inner, ctx->cfg.approx_activation_iters,
+               !(ctx->cfg.flags & LSE_FLAG_NO_CLUSTER)};
   const FitOut fo{out->theta, out->gamma, (c128*)out->alpha, out->K, out->beta, out->objective, out->iters,
                   out->n_evals, out->n_grid, out->status};
   const cudaError_t e = launch_fit(p->prec, y_d, (const InstDesc*)p->desc.p, p->B, p->Nmax, p->Lmax, fc, tables(ctx),

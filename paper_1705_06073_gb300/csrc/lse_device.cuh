@@ -154,6 +154,7 @@ struct LevShared {
   double logdet; // ln|C| (double-float recursion: result for the whole block)
   int expo;
   int status;    // 0 ok, 1 non-positive / non-finite pivot
+  int ctrl[2];   // cluster recursion: go / stop word of the last two barriers
 };
 
 struct LevResult {

@@ -132,57 +132,232 @@ __device__ __forceinline__ void lev_acc(LevAcc& A, f2 r, f2 i, float4 c4) {
   acc_prod(A.S3, A.E3, i, cr);
 }
 
-// One pair (i, j = n - i) of an order: a_i + k conj(a_j) and a_j + k conj(a_i)
-// from the loaded old values, stored where st_i / st_j, and both new values'
-// products with their column entries (ci4 for entry i, cj4 for entry j; a
-// zero entry adds exactly nothing) accumulated into A.
-__device__ __forceinline__ void lev_pair(float4* a, float4 ai, float4 aj, f2 kr, f2 ki, int i, int j, bool st_i,
-                                         bool st_j, float4 ci4, float4 cj4, LevAcc& A) {
-  const f2 air = re_of(ai), aii = im_of(ai), ajr = re_of(aj), aji = im_of(aj);
-  const f2 nir = axpy2f(air, kr, ajr, ki, aji);
-  const f2 nii = axpy2f(aii, ki, ajr, neg(kr), aji);
-  const f2 njr = axpy2f(ajr, kr, air, ki, aii);
-  const f2 nji = axpy2f(aji, ki, air, neg(kr), aii);
-  if (st_i) a[i] = pack(nir, nii);
-  if (st_j) a[j] = pack(njr, nji);
-  lev_acc(A, nir, nii, ci4);
-  lev_acc(A, njr, nji, cj4);
-}
-
 // barrier over the first NTL threads of the block (named barrier 1)
 template <int NTL>
 __device__ __forceinline__ void lev_bar() {
   asm volatile("bar.sync 1, %0;" ::"n"(NTL) : "memory");
 }
 
+// ---- thread-block clusters (two blocks of a cluster share one recursion) ----
+__device__ __forceinline__ unsigned cluster_ctarank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// every thread of every block of the cluster; release/acquire at cluster scope
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// address of the same shared-memory object in block `rank` of the cluster
+__device__ __forceinline__ unsigned cluster_addr(const void* p, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((unsigned)__cvta_generic_to_shared(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_cluster(unsigned addr, float4 v) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ float4 ld_cluster(unsigned addr) {
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(addr)
+               : "memory");
+  return v;
+}
+
+// One pair (i, j = n - i) of an order: a_i + k conj(a_j) and a_j + k conj(a_i)
+// from the loaded old values, stored where st_i / st_j (C = 2: also into the
+// other block's copy of a at peer_a), and both new values' products with
+// their column entries (ci4 for entry i, cj4 for entry j; a zero entry adds
+// exactly nothing) accumulated into A.
+template <int C>
+__device__ __forceinline__ void lev_pair(float4* a, unsigned peer_a, float4 ai, float4 aj, f2 kr, f2 ki, int i, int j,
+                                         bool st_i, bool st_j, float4 ci4, float4 cj4, LevAcc& A) {
+  const f2 air = re_of(ai), aii = im_of(ai), ajr = re_of(aj), aji = im_of(aj);
+  const f2 nir = axpy2f(air, kr, ajr, ki, aji);
+  const f2 nii = axpy2f(aii, ki, ajr, neg(kr), aji);
+  const f2 njr = axpy2f(ajr, kr, air, ki, aii);
+  const f2 nji = axpy2f(aji, ki, air, neg(kr), aii);
+  if (st_i) {
+    const float4 v = pack(nir, nii);
+    a[i] = v;
+    if constexpr (C == 2) st_cluster(peer_a + 16u * (unsigned)i, v);
+  }
+  if (st_j) {
+    const float4 v = pack(njr, nji);
+    a[j] = v;
+    if constexpr (C == 2) st_cluster(peer_a + 16u * (unsigned)j, v);
+  }
+  lev_acc(A, nir, nii, ci4);
+  lev_acc(A, njr, nji, cj4);
+}
+
+constexpr int kLevGo = 1, kLevStop = 2;
+
 // ---------------------------------------------------------------------------
-// The Levinson-Durbin recursion of block_levinson (same orders, same update of
-// every pair (i, n-i) fused with the next inner product), with the vectors,
-// the reflection coefficient, the pivot and the running product of pivots all
-// in double-float on the FP32 pipes.  The first column is scaled by 1/c_0 so
-// that every value stays near unit magnitude; pivots and ln|C| are returned in
-// the unscaled units.
-//
-// Only the first NTL = 128 threads (one warp per SM sub-partition) run the
-// orders; the rest of the block waits at the closing barrier.  Every order
-// ends with each warp's partial inner product in a double-buffered shared slot
-// and one barrier among those threads; then every thread sums the NTL/32 slots
-// in the same fixed tree and forms the next reflection coefficient itself, so
-// all of them hold bit-identical scalars.  The redundant per-order scalar work
-// is paid per warp, which is why fewer, busier warps win: at N = 4096 four
-// warps ran the recursion about 13% faster than eight.
-// Each thread takes two pairs per step without branches (a missing pair reads
-// c[0], stores nothing and accumulates zeros), and the pivot of the order,
-// which needs only k_n, is formed in the same straight-line block as the first
-// two pairs so that its dependency chain overlaps their arithmetic.
-// c: FP64 first column, converted in place to double-float (same 16 bytes per
-// element); a: output predictor in FP64.  red: 2*NTL/32 float4 of shared
-// memory; sh: receives the results for the threads that did not take part.
+// The orders of the double-float Levinson-Durbin recursion (the same orders
+// and the same update of every pair (i, n-i) fused with the next inner product
+// as block_levinson), run by the first NTL threads of C blocks (C = 1: one
+// block; C = 2: the two blocks of a cluster, each holding a full copy of c
+// and a in its own shared memory).  The pairs are dealt to the C * NTL
+// threads; a thread takes two pairs per step without branches (a missing pair
+// reads c[0], stores nothing and accumulates zeros).  Every order ends with
+// each warp's partial inner product in a double-buffered slot (C = 2: written
+// into both blocks) and one barrier over the participating threads (C = 2: a
+// cluster barrier, which also orders the mirrored stores of a); then every
+// thread sums the C * NTL / 32 slots in the same fixed tree and forms the next
+// reflection coefficient itself, so all of them hold bit-identical scalars
+// and leave the loop together.  The pivot of the order, which needs only k_n,
+// is formed in the same straight-line block as the first two pairs so that
+// its dependency chain overlaps their arithmetic.
+// c, a: double-float in shared memory (c scaled by 1/c_0, a[0] = 1, rest 0);
+// red: 2 * C * NTL / 32 float4.  C = 2: before every cluster barrier thread 0
+// writes sh->ctrl[barrier index & 1] (kLevGo, or kLevStop before the last one)
+// for the block's other threads (lev_shadow).  Thread 0 leaves the status,
+// pivot delta_{N-1} and ln|C| (unscaled) in sh.
 // ---------------------------------------------------------------------------
-template <int NT, int NTL = 128>
-__device__ LevResult block_levinson_df(c128* c64, c128* a64, int N, float4* red, LevShared* sh) {
-  static_assert(NTL % 32 == 0 && NTL <= NT, "recursion threads");
+template <int NTL, int C>
+__device__ void lev_orders(const float4* c, float4* a, int N, double c0, float4* red, LevShared* sh, unsigned rank) {
   constexpr int NW = NTL / 32;
+  constexpr int V = C * NTL;  // threads sharing the pairs
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int vt = threadIdx.x + NTL * (int)rank;
+  unsigned peer_a = 0, peer_red = 0;
+  if constexpr (C == 2) {
+    peer_a = cluster_addr(a, rank ^ 1u);
+    peer_red = cluster_addr(red, rank ^ 1u);
+  }
+  f2 kr{0.f, 0.f}, ki{0.f, 0.f};
+  if (N > 1) {
+    const float4 c1 = c[1];
+    kr = neg(re_of(c1));
+    ki = neg(im_of(c1));
+  }
+  f2 delta{1.f, 0.f}, mant{1.f, 0.f};
+  int expo = 0;
+  int bad = !(c0 > 0.0 && isfinite(c0));
+  int bidx = 0;  // cluster barriers passed
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int n = 1; n < N && !bad; ++n) {
+    const bool more = (n + 1) < N;
+    LevAcc A{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    f2 dn, inv_dn;
+    {
+      const int i0 = vt, i1 = vt + V;
+      const bool v0 = 2 * i0 <= n, v1 = 2 * i1 <= n;
+      const int ia = v0 ? i0 : 0, ib = v1 ? i1 : 0;
+      const int ja = v0 ? n - ia : 0, jb = v1 ? n - ib : 0;
+      const float4* pa = v0 ? a : c;
+      const float4* pb = v1 ? a : c;
+      const float4 aa_i = pa[ia], aa_j = pa[ja], ab_i = pb[ib], ab_j = pb[jb];
+      const bool wa_i = v0 && more, wa_j = wa_i && ja != ia, wb_i = v1 && more, wb_j = wb_i && jb != ib;
+      const float4 ca_i = c[wa_i ? n + 1 - ia : 0], ca_j = c[wa_j ? ia + 1 : 0];
+      const float4 cb_i = c[wb_i ? n + 1 - ib : 0], cb_j = c[wb_j ? ib + 1 : 0];
+      // pivot of this order, delta_n = delta_{n-1} (1 - |k_n|^2), and 1/delta_n
+      float p1, q1, p2, q2;
+      prod_terms(kr, kr, p1, q1);
+      prod_terms(ki, ki, p2, q2);
+      const f2 k2a = two_sum(p1, p2);
+      const f2 k2 = two_sum(k2a.h, __fadd_rn(__fadd_rn(q1, q2), k2a.l));
+      dn = mul(delta, sub(f2{1.f, 0.f}, k2));
+      inv_dn = recip(dn);
+      lev_pair<C>(a, peer_a, aa_i, aa_j, kr, ki, ia, ja, v0, v0 && ja != ia, wa_i ? ca_i : z4, wa_j ? ca_j : z4, A);
+      lev_pair<C>(a, peer_a, ab_i, ab_j, kr, ki, ib, jb, v1, v1 && jb != ib, wb_i ? cb_i : z4, wb_j ? cb_j : z4, A);
+    }
+    for (int ia = vt + 2 * V; 2 * ia <= n; ia += 2 * V) {
+      const int i1 = ia + V;
+      const bool v1 = 2 * i1 <= n;
+      const int ib = v1 ? i1 : 0;
+      const int ja = n - ia, jb = v1 ? n - ib : 0;
+      const float4* pb = v1 ? a : c;
+      const float4 aa_i = a[ia], aa_j = a[ja], ab_i = pb[ib], ab_j = pb[jb];
+      const bool wa_j = more && ja != ia, wb_i = v1 && more, wb_j = wb_i && jb != ib;
+      const float4 ca_i = c[more ? n + 1 - ia : 0], ca_j = c[wa_j ? ia + 1 : 0];
+      const float4 cb_i = c[wb_i ? n + 1 - ib : 0], cb_j = c[wb_j ? ib + 1 : 0];
+      lev_pair<C>(a, peer_a, aa_i, aa_j, kr, ki, ia, ja, true, ja != ia, more ? ca_i : z4, wa_j ? ca_j : z4, A);
+      lev_pair<C>(a, peer_a, ab_i, ab_j, kr, ki, ib, jb, v1, v1 && jb != ib, wb_i ? cb_i : z4, wb_j ? cb_j : z4, A);
+    }
+    acc_merge(A.S0, A.E0, A.S1, A.E1);
+    acc_merge(A.S2, A.E2, A.S3, A.E3);
+    float S0 = A.S0, E0 = A.E0, S2 = A.S2, E2 = A.E2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float sr = __shfl_xor_sync(0xffffffffu, S0, o), er = __shfl_xor_sync(0xffffffffu, E0, o);
+      const float si = __shfl_xor_sync(0xffffffffu, S2, o), ei = __shfl_xor_sync(0xffffffffu, E2, o);
+      acc_merge(S0, E0, sr, er);
+      acc_merge(S2, E2, si, ei);
+    }
+    float4* slot = red + (n & 1) * C * NW;
+    if (lane == 0) {
+      const float4 v = make_float4(S0, E0, S2, E2);
+      const int si = (int)rank * NW + warp;
+      slot[si] = v;
+      if constexpr (C == 2) st_cluster(peer_red + 16u * (unsigned)((n & 1) * C * NW + si), v);
+    }
+    if constexpr (C == 2) {
+      if (threadIdx.x == 0) sh->ctrl[bidx & 1] = kLevGo;
+      cluster_barrier();
+      ++bidx;
+    } else {
+      lev_bar<NTL>();
+    }
+    // the same fixed tree over the slots in every thread
+    float4 v[C * NW];
+#pragma unroll
+    for (int w = 0; w < C * NW; ++w) v[w] = slot[w];
+#pragma unroll
+    for (int st = 1; st < C * NW; st <<= 1) {
+#pragma unroll
+      for (int w = 0; w < C * NW; w += 2 * st) {
+        acc_merge(v[w].x, v[w].y, v[w + st].x, v[w + st].y);
+        acc_merge(v[w].z, v[w].w, v[w + st].z, v[w + st].w);
+      }
+    }
+    const float s0 = v[0].x, e0 = v[0].y, s1 = v[0].z, e1 = v[0].w;
+    if (!(dn.h > 0.f) || !isfinite(dn.h) || !isfinite(s0) || !isfinite(s1)) {
+      bad = 1;
+      break;
+    }
+    delta = dn;
+    // running product of the pivots, kept in [0.5, 1) with a separate exponent
+    const f2 m = mul(mant, dn);
+    int ex;
+    const float mh = frexpf(m.h, &ex);
+    mant = f2{mh, ldexpf(m.l, -ex)};
+    expo += ex;
+    if (more) {
+      const f2 er = two_sum(s0, e0), ei = two_sum(s1, e1);
+      kr = neg(mul(er, inv_dn));
+      ki = neg(mul(ei, inv_dn));
+    }
+  }
+  if constexpr (C == 2) {
+    if (threadIdx.x == 0) sh->ctrl[bidx & 1] = kLevStop;
+    cluster_barrier();
+  }
+  if (threadIdx.x == 0) {
+    sh->status = bad;
+    sh->delta = to_d(delta) * c0;
+    sh->logdet = log(to_d(mant)) + expo * 0.69314718055994530942 + (double)N * log(c0);
+  }
+}
+
+// The threads of a block that take no pairs in a cluster recursion: they pass
+// the same cluster barriers as the others (a cluster barrier counts every
+// thread of both blocks) and stop after the one announced by kLevStop.
+__device__ __forceinline__ void lev_shadow(const LevShared* sh) {
+  for (int bidx = 0;; ++bidx) {
+    cluster_barrier();
+    if (((volatile const int*)sh->ctrl)[bidx & 1] == kLevStop) break;
+  }
+}
+
+// c (FP64 first column, in shared memory) -> double-float in place, scaled by
+// 1/c_0; a <- e_0.  Returns c_0.
+template <int NT>
+__device__ double lev_prologue(c128* c64, c128* a64, int N) {
   float4* c = reinterpret_cast<float4*>(c64);
   float4* a = reinterpret_cast<float4*>(a64);
   const double c0 = c64[0].re;
@@ -194,117 +369,72 @@ __device__ LevResult block_levinson_df(c128* c64, c128* a64, int N, float4* red,
     a[i] = make_float4(i == 0 ? 1.f : 0.f, 0.f, 0.f, 0.f);
   }
   __syncthreads();
-  if (threadIdx.x < NTL) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    f2 kr{0.f, 0.f}, ki{0.f, 0.f};
-    if (N > 1) {
-      const float4 c1 = c[1];
-      kr = neg(re_of(c1));
-      ki = neg(im_of(c1));
-    }
-    f2 delta{1.f, 0.f}, mant{1.f, 0.f};
-    int expo = 0;
-    int bad = !(c0 > 0.0 && isfinite(c0));
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int n = 1; n < N && !bad; ++n) {
-      const bool more = (n + 1) < N;
-      LevAcc A{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      f2 dn, inv_dn;
-      {
-        const int i0 = threadIdx.x, i1 = threadIdx.x + NTL;
-        const bool v0 = 2 * i0 <= n, v1 = 2 * i1 <= n;
-        const int ia = v0 ? i0 : 0, ib = v1 ? i1 : 0;
-        const int ja = v0 ? n - ia : 0, jb = v1 ? n - ib : 0;
-        const float4* pa = v0 ? a : c;
-        const float4* pb = v1 ? a : c;
-        const float4 aa_i = pa[ia], aa_j = pa[ja], ab_i = pb[ib], ab_j = pb[jb];
-        const bool wa_i = v0 && more, wa_j = wa_i && ja != ia, wb_i = v1 && more, wb_j = wb_i && jb != ib;
-        const float4 ca_i = c[wa_i ? n + 1 - ia : 0], ca_j = c[wa_j ? ia + 1 : 0];
-        const float4 cb_i = c[wb_i ? n + 1 - ib : 0], cb_j = c[wb_j ? ib + 1 : 0];
-        // pivot of this order, delta_n = delta_{n-1} (1 - |k_n|^2), and 1/delta_n
-        float p1, q1, p2, q2;
-        prod_terms(kr, kr, p1, q1);
-        prod_terms(ki, ki, p2, q2);
-        const f2 k2a = two_sum(p1, p2);
-        const f2 k2 = two_sum(k2a.h, __fadd_rn(__fadd_rn(q1, q2), k2a.l));
-        dn = mul(delta, sub(f2{1.f, 0.f}, k2));
-        inv_dn = recip(dn);
-        lev_pair(a, aa_i, aa_j, kr, ki, ia, ja, v0, v0 && ja != ia, wa_i ? ca_i : z4, wa_j ? ca_j : z4, A);
-        lev_pair(a, ab_i, ab_j, kr, ki, ib, jb, v1, v1 && jb != ib, wb_i ? cb_i : z4, wb_j ? cb_j : z4, A);
-      }
-      for (int ia = threadIdx.x + 2 * NTL; 2 * ia <= n; ia += 2 * NTL) {
-        const int i1 = ia + NTL;
-        const bool v1 = 2 * i1 <= n;
-        const int ib = v1 ? i1 : 0;
-        const int ja = n - ia, jb = v1 ? n - ib : 0;
-        const float4* pb = v1 ? a : c;
-        const float4 aa_i = a[ia], aa_j = a[ja], ab_i = pb[ib], ab_j = pb[jb];
-        const bool wa_j = more && ja != ia, wb_i = v1 && more, wb_j = wb_i && jb != ib;
-        const float4 ca_i = c[more ? n + 1 - ia : 0], ca_j = c[wa_j ? ia + 1 : 0];
-        const float4 cb_i = c[wb_i ? n + 1 - ib : 0], cb_j = c[wb_j ? ib + 1 : 0];
-        lev_pair(a, aa_i, aa_j, kr, ki, ia, ja, true, ja != ia, more ? ca_i : z4, wa_j ? ca_j : z4, A);
-        lev_pair(a, ab_i, ab_j, kr, ki, ib, jb, v1, v1 && jb != ib, wb_i ? cb_i : z4, wb_j ? cb_j : z4, A);
-      }
-      acc_merge(A.S0, A.E0, A.S1, A.E1);
-      acc_merge(A.S2, A.E2, A.S3, A.E3);
-      float S0 = A.S0, E0 = A.E0, S2 = A.S2, E2 = A.E2;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float sr = __shfl_xor_sync(0xffffffffu, S0, o), er = __shfl_xor_sync(0xffffffffu, E0, o);
-        const float si = __shfl_xor_sync(0xffffffffu, S2, o), ei = __shfl_xor_sync(0xffffffffu, E2, o);
-        acc_merge(S0, E0, sr, er);
-        acc_merge(S2, E2, si, ei);
-      }
-      float4* slot = red + (n & 1) * NW;
-      if (lane == 0) slot[warp] = make_float4(S0, E0, S2, E2);
-      lev_bar<NTL>();
-      // the same fixed tree over the slots in every thread
-      float4 v[NW];
-#pragma unroll
-      for (int w = 0; w < NW; ++w) v[w] = slot[w];
-#pragma unroll
-      for (int st = 1; st < NW; st <<= 1) {
-#pragma unroll
-        for (int w = 0; w < NW; w += 2 * st) {
-          acc_merge(v[w].x, v[w].y, v[w + st].x, v[w + st].y);
-          acc_merge(v[w].z, v[w].w, v[w + st].z, v[w + st].w);
-        }
-      }
-      const float s0 = v[0].x, e0 = v[0].y, s1 = v[0].z, e1 = v[0].w;
-      if (!(dn.h > 0.f) || !isfinite(dn.h) || !isfinite(s0) || !isfinite(s1)) {
-        bad = 1;
-        break;
-      }
-      delta = dn;
-      // running product of the pivots, kept in [0.5, 1) with a separate exponent
-      const f2 m = mul(mant, dn);
-      int ex;
-      const float mh = frexpf(m.h, &ex);
-      mant = f2{mh, ldexpf(m.l, -ex)};
-      expo += ex;
-      if (more) {
-        const f2 er = two_sum(s0, e0), ei = two_sum(s1, e1);
-        kr = neg(mul(er, inv_dn));
-        ki = neg(mul(ei, inv_dn));
-      }
-    }
-    if (threadIdx.x == 0) {
-      sh->status = bad;
-      sh->delta = to_d(delta) * c0;
-      sh->logdet = log(to_d(mant)) + expo * 0.69314718055994530942 + (double)N * log(c0);
-    }
-  }
-  __syncthreads();
+  return c0;
+}
+
+// a (double-float) -> FP64 in place; results of lev_orders from sh
+template <int NT>
+__device__ LevResult lev_epilogue(c128* a64, int N, const LevShared* sh) {
+  const float4* a = reinterpret_cast<const float4*>(a64);
   LevResult r;
   r.status = sh->status;
   r.delta_last = sh->delta;
   r.logdet = sh->logdet;
-  // back to FP64 in place
   for (int i = threadIdx.x; i < N; i += NT) {
     const float4 v = a[i];
     a64[i] = mk(to_d(re_of(v)), to_d(im_of(v)));
   }
   __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// The double-float Levinson-Durbin recursion in one block: the orders run on
+// the first NTL = 128 threads (one warp per SM sub-partition) and the rest of
+// the block waits at the closing barrier.  The per-order reduction and scalar
+// work is paid per warp, which is why fewer, busier warps win: at N = 4096
+// four warps ran the recursion about 13% faster than eight.
+// c: FP64 first column, converted in place to double-float (same 16 bytes per
+// element); a: output predictor in FP64.  red: 2*NTL/32 float4 of shared
+// memory; sh: carries the results to the threads that did not take part.
+// ---------------------------------------------------------------------------
+template <int NT, int NTL = 128>
+__device__ __noinline__ LevResult block_levinson_df(c128* c64, c128* a64, int N, float4* red, LevShared* sh) {
+  static_assert(NTL % 32 == 0 && NTL <= NT, "recursion threads");
+  const double c0 = lev_prologue<NT>(c64, a64, N);
+  if (threadIdx.x < NTL)
+    lev_orders<NTL, 1>(reinterpret_cast<const float4*>(c64), reinterpret_cast<float4*>(a64), N, c0, red, sh, 0u);
+  __syncthreads();
+  return lev_epilogue<NT>(a64, N, sh);
+}
+
+// ---------------------------------------------------------------------------
+// The same recursion shared by the two blocks of a cluster (each on its own
+// SM), called by every thread of both blocks with the same N and c_0.  c: the
+// double-float column (scaled by 1/c_0) already in this block's shared memory;
+// a: this block's copy of the predictor (the pairs each block updates are
+// stored into both copies).  Returns with a complete in both blocks, still in
+// double-float; the caller converts what it needs.  One cluster barrier per
+// order (about 0.2 us on GB300) against half the pair work per SM.
+// Not inlined: the two blocks of a cluster then run one copy of the code.
+// Two inlined copies (one in each block's caller) measured 16% slower on the
+// whole fit, with instruction-fetch stalls as the top stall reason; the two
+// SMs of a cluster evidently share an instruction cache level.
+// ---------------------------------------------------------------------------
+template <int NT, int NTL = 128>
+__device__ __noinline__ LevResult cluster_levinson_df(const c128* c64, c128* a64, int N, double c0, float4* red, LevShared* sh) {
+  static_assert(NTL % 32 == 0 && NTL <= NT, "recursion threads");
+  const unsigned rank = cluster_ctarank();
+  float4* a = reinterpret_cast<float4*>(a64);
+  for (int i = threadIdx.x; i < N; i += NT) a[i] = make_float4(i == 0 ? 1.f : 0.f, 0.f, 0.f, 0.f);
+  cluster_barrier();  // both copies initialised before any mirrored store
+  if (threadIdx.x < NTL) lev_orders<NTL, 2>(reinterpret_cast<const float4*>(c64), a, N, c0, red, sh, rank);
+  else lev_shadow(sh);
+  __syncthreads();
+  LevResult r;
+  r.status = sh->status;
+  r.delta_last = sh->delta;
+  r.logdet = sh->logdet;
   return r;
 }
 

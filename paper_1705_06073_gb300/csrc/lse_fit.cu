@@ -45,12 +45,28 @@ constexpr int kSmemBytes = 200 * 1024;
 constexpr double kEpsL = 2.220446049250313e-16;
 constexpr int kST_OK = 0, kST_NUMERIC = 4, kST_NOTCONV = 5;
 
+// whether the recursion's c and a (2N complex doubles) and the first-column
+// tables fit in the block's dynamic shared memory
+__host__ __device__ inline bool lev_in_smem(int N) {
+  int S, H;
+  first_column_split(N, S, H);
+  const size_t tab_bytes = sizeof(c128) * kFirstColumnChunk * (S + H);
+  return (2 * sizeof(c128) * (size_t)N + tab_bytes) <= (size_t)kSmemBytes;
+}
+
 template <int kNT>
 struct FitShared {
   c128 red[kNT];
   MinLoc ml[kNT / 32];
   double dred[kNT / 32];
   LevShared lev;
+  // cluster mode: the recursion request the first block of a cluster writes
+  // into the second block's copy before the barrier that releases it
+  // (op 1: recursion of order N with c_0; op 0: no more work)
+  struct alignas(16) {
+    int op, N;
+    double c0;
+  } cmd;
   // instance state (written by thread 0, read by all after a barrier)
   int inst, K, status, n_evals, n_grid, cand_count, flag;
   double beta, zeta, eps_beta, tau;
@@ -156,6 +172,7 @@ struct FitArgs {
   char* ws;
   size_t ws_bytes;
   int* counter;
+  int cluster;  // 1: launched as clusters of two blocks (double-float path)
 };
 
 __device__ __forceinline__ double prior_term(int K, int N, double zeta) {
@@ -198,8 +215,12 @@ struct Fitter {
     const double beta = sh->beta;
     block_first_column<kNT>(lev_c, th, ga, K, beta, N, tables);
     LevResult lr;
-    if constexpr (PREC == 2) lr = block_levinson_df<kNT>(lev_c, lev_a, N, (float4*)sh->red, &sh->lev);
-    else lr = block_levinson<kNT>(lev_c, lev_a, N, sh->red, &sh->lev);
+    if constexpr (PREC == 2) {
+      if (A->cluster && lev_smem) lr = cluster_levinson();
+      else lr = block_levinson_df<kNT>(lev_c, lev_a, N, (float4*)sh->red, &sh->lev);
+    } else {
+      lr = block_levinson<kNT>(lev_c, lev_a, N, sh->red, &sh->lev);
+    }
     if (threadIdx.x == 0) sh->n_evals++;
     if (lr.status) {
       __syncthreads();
@@ -229,6 +250,22 @@ struct Fitter {
     }
     if (want_sums && K > 0) compute_sums(th, K);
     return 0;
+  }
+
+  // The recursion shared with the second block of the cluster: convert c,
+  // hand the request over, run the orders together, and convert a back.
+  __device__ LevResult cluster_levinson() {
+    const double c0 = lev_prologue<kNT>(lev_c, lev_a, N);
+    if (threadIdx.x == 0) send_cmd(1, N, c0);
+    cluster_barrier();
+    cluster_levinson_df<kNT>(lev_c, lev_a, N, c0, (float4*)sh->red, &sh->lev);
+    return lev_epilogue<kNT>(lev_a, N, &sh->lev);
+  }
+  __device__ void send_cmd(int op, int n, double c0) const {
+    const unsigned dst = cluster_addr(&sh->cmd, 1u);
+    const float4 v = make_float4(__int_as_float(op), __int_as_float(n), __int_as_float(__double2loint(c0)),
+                                 __int_as_float(__double2hiint(c0)));
+    st_cluster(dst, v);
   }
 
   // The Newton sums keep FP64 accuracy on every path (FP64, or double-float
@@ -608,10 +645,7 @@ struct Fitter {
     }
     const double yy = block_sum<kNT>(part, sh->dred);
     // Levinson arrays in shared memory when they fit
-    int S, H;
-    first_column_split(N, S, H);
-    const size_t tab_bytes = sizeof(c128) * kFirstColumnChunk * (S + H);
-    lev_smem = (2 * sizeof(c128) * (size_t)N + tab_bytes) <= (size_t)kSmemBytes;
+    lev_smem = lev_in_smem(N);
     if (lev_smem) {
       lev_c = (c128*)dsm;
       lev_a = lev_c + N;
@@ -740,16 +774,46 @@ struct Fitter {
   }
 };
 
+// The second block of a cluster: it waits for recursion requests from the
+// first block and runs its half of each (double-float path only).
+template <int kNT>
+__device__ void cluster_helper(FitShared<kNT>& sh, char* dsm) {
+  for (;;) {
+    cluster_barrier();  // a request (or the end) is in sh.cmd
+    const int op = sh.cmd.op, n = sh.cmd.N;
+    const double c0 = sh.cmd.c0;
+    if (op != 1) break;
+    c128* c = reinterpret_cast<c128*>(dsm);
+    c128* a = c + n;
+    const unsigned src = cluster_addr(c, 0u);
+    float4* c4 = reinterpret_cast<float4*>(c);
+    for (int i = threadIdx.x; i < n; i += kNT) c4[i] = ld_cluster(src + 16u * (unsigned)i);
+    __syncthreads();
+    cluster_levinson_df<kNT>(c, a, n, c0, (float4*)sh.red, &sh.lev);
+  }
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(threads_for<PREC>(), 1) fit_kernel(FitArgs args) {
   using TG = typename Fitter<PREC>::TG;
   __shared__ FitShared<threads_for<PREC>()> sh;
   extern __shared__ __align__(16) char dsm[];
+  int unit = blockIdx.x;  // workspace index
+  if constexpr (PREC == 2) {
+    if (args.cluster) {
+      cluster_barrier();  // both blocks running before any shared-memory store between them
+      if (cluster_ctarank() != 0) {
+        cluster_helper<threads_for<PREC>()>(sh, dsm);
+        return;
+      }
+      unit = blockIdx.x >> 1;
+    }
+  }
   Fitter<PREC> F;
   F.sh = &sh;
   F.dsm = dsm;
   F.A = &args;
-  F.w = carve<TG>(args.ws + (size_t)blockIdx.x * args.ws_bytes, args.Nmax, args.Lmax);
+  F.w = carve<TG>(args.ws + (size_t)unit * args.ws_bytes, args.Nmax, args.Lmax);
   F.tw64 = Twiddles<double>{args.tab.tw64, args.tab.log2max};
   if constexpr (PREC != 0) F.twg = Twiddles<TG>{(const cx<TG>*)args.tab.tw32, args.tab.log2max};
   else F.twg = Twiddles<TG>{(const cx<TG>*)args.tab.tw64, args.tab.log2max};
@@ -760,6 +824,12 @@ __global__ void __launch_bounds__(threads_for<PREC>(), 1) fit_kernel(FitArgs arg
     __syncthreads();
     if (b >= args.B) break;
     F.run(b);
+  }
+  if constexpr (PREC == 2) {
+    if (args.cluster) {  // release the second block
+      if (threadIdx.x == 0) F.send_cmd(0, 0, 0.0);
+      cluster_barrier();
+    }
   }
 }
 
@@ -774,6 +844,21 @@ template <int PREC>
 static cudaError_t launch_prec(const FitArgs& a, int grid, cudaStream_t stream) {
   cudaError_t e = cudaFuncSetAttribute(fit_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   if (e != cudaSuccess) return e;
+  if (a.cluster) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(2 * grid);
+    lc.blockDim = dim3(threads_for<PREC>());
+    lc.dynamicSmemBytes = kSmemBytes;
+    lc.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, fit_kernel<PREC>, a);
+  }
   fit_kernel<PREC><<<grid, threads_for<PREC>(), kSmemBytes, stream>>>(a);
   return cudaGetLastError();
 }
@@ -793,6 +878,16 @@ cudaError_t launch_fit(int prec, const float* y, const InstDesc* inst, int B, in
   a.ws = (char*)ws;
   a.ws_bytes = fit_workspace_bytes(Nmax, Lmax, prec);
   a.counter = counter;
+  // Clusters of two blocks (the second one runs half of every recursion)
+  // when the batch leaves at least one spare SM per instance and the
+  // recursion of every instance runs in shared memory.
+  a.cluster = 0;
+  if (prec == 2 && cfg.cluster && lev_in_smem(Nmax)) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && 2 * grid <= sms)
+      a.cluster = 1;
+  }
   switch (prec) {
     case 0: return launch_prec<0>(a, grid, stream);
     case 1: return launch_prec<1>(a, grid, stream);

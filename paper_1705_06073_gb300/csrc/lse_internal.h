@@ -28,6 +28,7 @@ struct InstDesc {
 struct FitConfig {
   double tau;
   int max_outer, max_inner, approx_iters;
+  int cluster;  // clusters of two blocks allowed (double-float path)
 };
 
 // Device outputs of the fit kernel (see lse_batch_out).

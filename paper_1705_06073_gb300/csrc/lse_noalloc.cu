@@ -121,7 +121,7 @@ LSE_API lse_status lse_fit_noalloc_d(const lse_config* cfg, const float* y_d, in
   if (cudaMemcpyAsync(d->desc, &h, sizeof(h), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemsetAsync(d->counter, 0, sizeof(int), st) != cudaSuccess)
     return set_err(LSE_ECUDA, "lse_fit_noalloc_d: staging the launch descriptor failed");
-  const FitConfig fc{c.tau, c.max_outer, c.max_inner, c.approx_activation_iters};
+  const FitConfig fc{c.tau, c.max_outer, c.max_inner, c.approx_activation_iters, !(c.flags & LSE_FLAG_NO_CLUSTER)};
   const FitOut fo{out->theta, out->gamma, (c128*)out->alpha, out->K, out->beta, out->objective, out->iters,
                   out->n_evals, out->n_grid, out->status};
   const Tables tab{d->tw64, d->tw32, kMaxLog2L};

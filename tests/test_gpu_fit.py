@@ -118,3 +118,28 @@ def test_fit_capacity_error(lse_mod):
         assert r["status"] == lse_mod.LSE_ECAPACITY and r["K"] == 8 and r["theta"] is None
     finally:
         lse_mod.lse_destroy(ctx)
+
+
+def test_cluster_recursion_matches_one_block():
+    """Double-float path: the same batch fitted with clusters of two blocks
+    (default for a batch smaller than half the SMs) and with one block per
+    instance (LSE_FLAG_NO_CLUSTER) gives the same fits to rounding: the two
+    differ only in the order the inner products of the recursion are summed."""
+    from paper_1705_06073_gb300 import build, lse
+    build.build()
+    specs = [(256, 8), (1000, 16), (2048, 32), (4096, 64), (37, 2), (600, 9), (3000, 40), (5000, 70)]
+    insts = [synth.make_instance(N, K, 20.0, 8100 + i) for i, (N, K) in enumerate(specs)]
+    res = {}
+    for flags in (0, lse.LSE_FLAG_NO_CLUSTER):
+        ctx = lse.lse_create(lse.lse_config_default(precision=lse.LSE_PREC_MIXED_DF, flags=flags))
+        try:
+            res[flags] = lse.lse_fit_batch(ctx, [i.y for i in insts])
+        finally:
+            lse.lse_destroy(ctx)
+    for a, b in zip(res[0], res[lse.LSE_FLAG_NO_CLUSTER]):
+        assert a["status"] == b["status"] and a["status"] in (0, lse.LSE_ENOTCONV)
+        assert a["K"] == b["K"] and a["n_evals"] == b["n_evals"] and a["iters"] == b["iters"]
+        if a["K"]:
+            assert np.all(wrapdist(a["theta"], b["theta"]) < 1e-9)
+            assert np.allclose(a["gamma"], b["gamma"], rtol=1e-8)
+        assert abs(a["beta"] - b["beta"]) <= 1e-9 * b["beta"]
