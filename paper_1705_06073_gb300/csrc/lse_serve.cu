@@ -8,9 +8,13 @@
 // whose device memory fits what the budget leaves, copies their inputs in
 // and launches one persistent fit kernel over them.  Requests that arrive
 // while other groups run start on another slot, so their work overlaps on
-// the device; every instance is computed by one thread block with the same
-// arithmetic as a lone lse_fit, so a result does not depend on the mix it
-// ran in.
+// the device.  Every instance is computed with the same arithmetic as a lone
+// lse_fit: one thread block per instance, or a two-block cluster on the
+// double-float path when the group is small enough (the two differ only in
+// the order the recursion's inner products are summed).  So a result does
+// not depend on the mix it ran in, bit for bit whenever the group and the
+// lone fit run in the same mode (always with LSE_FLAG_NO_CLUSTER), and to
+// rounding otherwise.
 #include <algorithm>
 #include <chrono>
 #include <cmath>

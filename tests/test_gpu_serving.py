@@ -1,6 +1,9 @@
 """Continuous batching (lse_serve_*): requests that arrive while others run
 are admitted as slots and memory free up, their work overlaps on the device,
-and every result equals the same request fitted alone."""
+and every result equals the same request fitted alone.  The requests here are
+small (N <= 512, groups of at most 5), so every group and every lone fit runs
+in the same mode (two-block clusters on the double-float path) and the
+results must agree bit for bit."""
 import time
 
 import numpy as np
