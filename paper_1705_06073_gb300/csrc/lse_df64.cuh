@@ -168,11 +168,11 @@ __device__ __forceinline__ float4 ld_cluster(unsigned addr) {
 }
 
 // One pair (i, j = n - i) of an order: a_i + k conj(a_j) and a_j + k conj(a_i)
-// from the loaded old values, stored where st_i / st_j (C = 2: also into the
+// from the loaded old values, stored where st_i / st_j (MIRROR: also into the
 // other block's copy of a at peer_a), and both new values' products with
 // their column entries (ci4 for entry i, cj4 for entry j; a zero entry adds
 // exactly nothing) accumulated into A.
-template <int C>
+template <bool MIRROR>
 __device__ __forceinline__ void lev_pair(float4* a, unsigned peer_a, float4 ai, float4 aj, f2 kr, f2 ki, int i, int j,
                                          bool st_i, bool st_j, float4 ci4, float4 cj4, LevAcc& A) {
   const f2 air = re_of(ai), aii = im_of(ai), ajr = re_of(aj), aji = im_of(aj);
@@ -183,15 +183,56 @@ __device__ __forceinline__ void lev_pair(float4* a, unsigned peer_a, float4 ai, 
   if (st_i) {
     const float4 v = pack(nir, nii);
     a[i] = v;
-    if constexpr (C == 2) st_cluster(peer_a + 16u * (unsigned)i, v);
+    if constexpr (MIRROR) st_cluster(peer_a + 16u * (unsigned)i, v);
   }
   if (st_j) {
     const float4 v = pack(njr, nji);
     a[j] = v;
-    if constexpr (C == 2) st_cluster(peer_a + 16u * (unsigned)j, v);
+    if constexpr (MIRROR) st_cluster(peer_a + 16u * (unsigned)j, v);
   }
   lev_acc(A, nir, nii, ci4);
   lev_acc(A, njr, nji, cj4);
+}
+
+// loads of the recursion's vectors: shared memory, or (G) global memory read
+// through L2 only, since other SMs of the cluster rewrite a between orders
+template <bool G>
+__device__ __forceinline__ float4 lev_ld(const float4* p) {
+  if constexpr (G) return __ldcg(p);
+  else return *p;
+}
+
+// Sum of NS double-float partial sums {S_re, E_re, S_im, E_im} in a fixed
+// pairwise tree (groups of at most 8, then the group totals), so that every
+// thread that calls it gets bit-identical totals.
+template <int NS>
+__device__ __forceinline__ float4 tree8(const float4* slot) {
+  static_assert(NS >= 1 && NS <= 8 && (NS & (NS - 1)) == 0, "tree of 1..8 slots");
+  float4 v[NS];
+#pragma unroll
+  for (int w = 0; w < NS; ++w) v[w] = slot[w];
+#pragma unroll
+  for (int st = 1; st < NS; st <<= 1) {
+#pragma unroll
+    for (int w = 0; w < NS; w += 2 * st) {
+      acc_merge(v[w].x, v[w].y, v[w + st].x, v[w + st].y);
+      acc_merge(v[w].z, v[w].w, v[w + st].z, v[w + st].w);
+    }
+  }
+  return v[0];
+}
+
+template <int NS>
+__device__ __forceinline__ float4 slot_total(const float4* slot) {
+  if constexpr (NS <= 8) {
+    return tree8<NS>(slot);
+  } else {
+    static_assert(NS % 8 == 0 && NS <= 64, "up to 64 slots");
+    float4 g[NS / 8];
+#pragma unroll
+    for (int k = 0; k < NS / 8; ++k) g[k] = tree8<8>(slot + 8 * k);
+    return tree8<NS / 8>(g);
+  }
 }
 
 constexpr int kLevGo = 1, kLevStop = 2;
@@ -199,39 +240,43 @@ constexpr int kLevGo = 1, kLevStop = 2;
 // ---------------------------------------------------------------------------
 // The orders of the double-float Levinson-Durbin recursion (the same orders
 // and the same update of every pair (i, n-i) fused with the next inner product
-// as block_levinson), run by the first NTL threads of C blocks (C = 1: one
-// block; C = 2: the two blocks of a cluster, each holding a full copy of c
-// and a in its own shared memory).  The pairs are dealt to the C * NTL
-// threads; a thread takes two pairs per step without branches (a missing pair
-// reads c[0], stores nothing and accumulates zeros).  Every order ends with
-// each warp's partial inner product in a double-buffered slot (C = 2: written
-// into both blocks) and one barrier over the participating threads (C = 2: a
-// cluster barrier, which also orders the mirrored stores of a); then every
-// thread sums the C * NTL / 32 slots in the same fixed tree and forms the next
-// reflection coefficient itself, so all of them hold bit-identical scalars
-// and leave the loop together.  The pivot of the order, which needs only k_n,
-// is formed in the same straight-line block as the first two pairs so that
-// its dependency chain overlaps their arithmetic.
-// c, a: double-float in shared memory (c scaled by 1/c_0, a[0] = 1, rest 0);
-// red: 2 * C * NTL / 32 float4.  C = 2: before every cluster barrier thread 0
-// writes sh->ctrl[barrier index & 1] (kLevGo, or kLevStop before the last one)
-// for the block's other threads (lev_shadow).  Thread 0 leaves the status,
-// pivot delta_{N-1} and ln|C| (unscaled) in sh.
+// as block_levinson), run by the first NTL threads of C blocks:
+//  - C = 1: one block, c and a in its shared memory;
+//  - C = 2, G = false: the two blocks of a cluster, each holding a full copy
+//    of c and a in its own shared memory; every stored entry is mirrored
+//    into the other copy;
+//  - G = true: the C blocks of a cluster share one c and a in global memory
+//    (large N), read through L2.
+// The pairs are dealt to the C * NTL threads; a thread takes two pairs per
+// step without branches (a missing pair reads c[0], stores nothing and
+// accumulates zeros).  Every order ends with each warp's partial inner
+// product in a double-buffered slot (C > 1: written into every block of the
+// cluster) and one barrier over the participating threads (C > 1: a cluster
+// barrier, whose release/acquire also orders the stores of a); then every
+// thread sums the C * NTL / 32 slots in the same fixed tree and forms the
+// next reflection coefficient itself, so all of them hold bit-identical
+// scalars and leave the loop together.  The pivot of the order, which needs
+// only k_n, is formed in the same straight-line block as the first two pairs
+// so that its dependency chain overlaps their arithmetic.
+// c, a: double-float (c scaled by 1/c_0, a[0] = 1, rest 0); red: 2 * C *
+// NTL / 32 float4 of shared memory.  C > 1: before every cluster barrier
+// thread 0 writes sh->ctrl[barrier index & 1] (kLevGo, or kLevStop before
+// the last one) for the block's threads that take no pairs (lev_shadow).
+// Thread 0 leaves the status, pivot delta_{N-1} and ln|C| (unscaled) in sh.
 // ---------------------------------------------------------------------------
-template <int NTL, int C>
+template <int NTL, int C, bool G = false>
 __device__ void lev_orders(const float4* c, float4* a, int N, double c0, float4* red, LevShared* sh, unsigned rank) {
   constexpr int NW = NTL / 32;
   constexpr int V = C * NTL;  // threads sharing the pairs
+  constexpr bool MIRROR = (C == 2) && !G;
+  static_assert(C == 1 || C == 2 || G, "shared-memory copies are mirrored between two blocks only");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int vt = threadIdx.x + NTL * (int)rank;
-  unsigned peer_a = 0, peer_red = 0;
-  if constexpr (C == 2) {
-    peer_a = cluster_addr(a, rank ^ 1u);
-    peer_red = cluster_addr(red, rank ^ 1u);
-  }
+  unsigned peer_a = 0;
+  if constexpr (MIRROR) peer_a = cluster_addr(a, rank ^ 1u);
   f2 kr{0.f, 0.f}, ki{0.f, 0.f};
   if (N > 1) {
-    const float4 c1 = c[1];
+    const float4 c1 = lev_ld<G>(c + 1);
     kr = neg(re_of(c1));
     ki = neg(im_of(c1));
   }
@@ -251,10 +296,11 @@ __device__ void lev_orders(const float4* c, float4* a, int N, double c0, float4*
       const int ja = v0 ? n - ia : 0, jb = v1 ? n - ib : 0;
       const float4* pa = v0 ? a : c;
       const float4* pb = v1 ? a : c;
-      const float4 aa_i = pa[ia], aa_j = pa[ja], ab_i = pb[ib], ab_j = pb[jb];
+      const float4 aa_i = lev_ld<G>(pa + ia), aa_j = lev_ld<G>(pa + ja), ab_i = lev_ld<G>(pb + ib),
+                   ab_j = lev_ld<G>(pb + jb);
       const bool wa_i = v0 && more, wa_j = wa_i && ja != ia, wb_i = v1 && more, wb_j = wb_i && jb != ib;
-      const float4 ca_i = c[wa_i ? n + 1 - ia : 0], ca_j = c[wa_j ? ia + 1 : 0];
-      const float4 cb_i = c[wb_i ? n + 1 - ib : 0], cb_j = c[wb_j ? ib + 1 : 0];
+      const float4 ca_i = lev_ld<G>(c + (wa_i ? n + 1 - ia : 0)), ca_j = lev_ld<G>(c + (wa_j ? ia + 1 : 0));
+      const float4 cb_i = lev_ld<G>(c + (wb_i ? n + 1 - ib : 0)), cb_j = lev_ld<G>(c + (wb_j ? ib + 1 : 0));
       // pivot of this order, delta_n = delta_{n-1} (1 - |k_n|^2), and 1/delta_n
       float p1, q1, p2, q2;
       prod_terms(kr, kr, p1, q1);
@@ -263,8 +309,8 @@ __device__ void lev_orders(const float4* c, float4* a, int N, double c0, float4*
       const f2 k2 = two_sum(k2a.h, __fadd_rn(__fadd_rn(q1, q2), k2a.l));
       dn = mul(delta, sub(f2{1.f, 0.f}, k2));
       inv_dn = recip(dn);
-      lev_pair<C>(a, peer_a, aa_i, aa_j, kr, ki, ia, ja, v0, v0 && ja != ia, wa_i ? ca_i : z4, wa_j ? ca_j : z4, A);
-      lev_pair<C>(a, peer_a, ab_i, ab_j, kr, ki, ib, jb, v1, v1 && jb != ib, wb_i ? cb_i : z4, wb_j ? cb_j : z4, A);
+      lev_pair<MIRROR>(a, peer_a, aa_i, aa_j, kr, ki, ia, ja, v0, v0 && ja != ia, wa_i ? ca_i : z4, wa_j ? ca_j : z4, A);
+      lev_pair<MIRROR>(a, peer_a, ab_i, ab_j, kr, ki, ib, jb, v1, v1 && jb != ib, wb_i ? cb_i : z4, wb_j ? cb_j : z4, A);
     }
     for (int ia = vt + 2 * V; 2 * ia <= n; ia += 2 * V) {
       const int i1 = ia + V;
@@ -272,12 +318,13 @@ __device__ void lev_orders(const float4* c, float4* a, int N, double c0, float4*
       const int ib = v1 ? i1 : 0;
       const int ja = n - ia, jb = v1 ? n - ib : 0;
       const float4* pb = v1 ? a : c;
-      const float4 aa_i = a[ia], aa_j = a[ja], ab_i = pb[ib], ab_j = pb[jb];
+      const float4 aa_i = lev_ld<G>(a + ia), aa_j = lev_ld<G>(a + ja), ab_i = lev_ld<G>(pb + ib),
+                   ab_j = lev_ld<G>(pb + jb);
       const bool wa_j = more && ja != ia, wb_i = v1 && more, wb_j = wb_i && jb != ib;
-      const float4 ca_i = c[more ? n + 1 - ia : 0], ca_j = c[wa_j ? ia + 1 : 0];
-      const float4 cb_i = c[wb_i ? n + 1 - ib : 0], cb_j = c[wb_j ? ib + 1 : 0];
-      lev_pair<C>(a, peer_a, aa_i, aa_j, kr, ki, ia, ja, true, ja != ia, more ? ca_i : z4, wa_j ? ca_j : z4, A);
-      lev_pair<C>(a, peer_a, ab_i, ab_j, kr, ki, ib, jb, v1, v1 && jb != ib, wb_i ? cb_i : z4, wb_j ? cb_j : z4, A);
+      const float4 ca_i = lev_ld<G>(c + (more ? n + 1 - ia : 0)), ca_j = lev_ld<G>(c + (wa_j ? ia + 1 : 0));
+      const float4 cb_i = lev_ld<G>(c + (wb_i ? n + 1 - ib : 0)), cb_j = lev_ld<G>(c + (wb_j ? ib + 1 : 0));
+      lev_pair<MIRROR>(a, peer_a, aa_i, aa_j, kr, ki, ia, ja, true, ja != ia, more ? ca_i : z4, wa_j ? ca_j : z4, A);
+      lev_pair<MIRROR>(a, peer_a, ab_i, ab_j, kr, ki, ib, jb, v1, v1 && jb != ib, wb_i ? cb_i : z4, wb_j ? cb_j : z4, A);
     }
     acc_merge(A.S0, A.E0, A.S1, A.E1);
     acc_merge(A.S2, A.E2, A.S3, A.E3);
@@ -294,9 +341,13 @@ __device__ void lev_orders(const float4* c, float4* a, int N, double c0, float4*
       const float4 v = make_float4(S0, E0, S2, E2);
       const int si = (int)rank * NW + warp;
       slot[si] = v;
-      if constexpr (C == 2) st_cluster(peer_red + 16u * (unsigned)((n & 1) * C * NW + si), v);
+      if constexpr (C > 1) {
+#pragma unroll
+        for (unsigned r = 1; r < (unsigned)C; ++r)
+          st_cluster(cluster_addr(slot + si, (rank + r) % (unsigned)C), v);
+      }
     }
-    if constexpr (C == 2) {
+    if constexpr (C > 1) {
       if (threadIdx.x == 0) sh->ctrl[bidx & 1] = kLevGo;
       cluster_barrier();
       ++bidx;
@@ -304,18 +355,8 @@ __device__ void lev_orders(const float4* c, float4* a, int N, double c0, float4*
       lev_bar<NTL>();
     }
     // the same fixed tree over the slots in every thread
-    float4 v[C * NW];
-#pragma unroll
-    for (int w = 0; w < C * NW; ++w) v[w] = slot[w];
-#pragma unroll
-    for (int st = 1; st < C * NW; st <<= 1) {
-#pragma unroll
-      for (int w = 0; w < C * NW; w += 2 * st) {
-        acc_merge(v[w].x, v[w].y, v[w + st].x, v[w + st].y);
-        acc_merge(v[w].z, v[w].w, v[w + st].z, v[w + st].w);
-      }
-    }
-    const float s0 = v[0].x, e0 = v[0].y, s1 = v[0].z, e1 = v[0].w;
+    const float4 tot = slot_total<C * NW>(slot);
+    const float s0 = tot.x, e0 = tot.y, s1 = tot.z, e1 = tot.w;
     if (!(dn.h > 0.f) || !isfinite(dn.h) || !isfinite(s0) || !isfinite(s1)) {
       bad = 1;
       break;
@@ -333,7 +374,7 @@ __device__ void lev_orders(const float4* c, float4* a, int N, double c0, float4*
       ki = neg(mul(ei, inv_dn));
     }
   }
-  if constexpr (C == 2) {
+  if constexpr (C > 1) {
     if (threadIdx.x == 0) sh->ctrl[bidx & 1] = kLevStop;
     cluster_barrier();
   }
@@ -430,6 +471,31 @@ __device__ __noinline__ LevResult cluster_levinson_df(const c128* c64, c128* a64
   cluster_barrier();  // both copies initialised before any mirrored store
   if (threadIdx.x < NTL) lev_orders<NTL, 2>(reinterpret_cast<const float4*>(c64), a, N, c0, red, sh, rank);
   else lev_shadow(sh);
+  __syncthreads();
+  LevResult r;
+  r.status = sh->status;
+  r.delta_last = sh->delta;
+  r.logdet = sh->logdet;
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// The recursion of a large instance shared by the C blocks of a cluster, with
+// c and a in global memory (the instance's workspace; L2-resident), called by
+// every thread of every block with the same arguments.  All NT threads of a
+// block take pairs.  c: double-float, scaled by 1/c_0 (written before the
+// cluster barrier that precedes this call); a is initialised here.  Returns
+// with a complete in global memory, still in double-float.  Not inlined, so
+// the blocks of a cluster run one copy of the code.
+// ---------------------------------------------------------------------------
+template <int NT, int C>
+__device__ __noinline__ LevResult cluster_levinson_global(const c128* c64, c128* a64, int N, double c0, float4* red,
+                                                          LevShared* sh) {
+  const unsigned rank = cluster_ctarank();
+  float4* a = reinterpret_cast<float4*>(a64);
+  for (int i = threadIdx.x + NT * (int)rank; i < N; i += NT * C) a[i] = make_float4(i == 0 ? 1.f : 0.f, 0.f, 0.f, 0.f);
+  cluster_barrier();  // a initialised (and c visible) in every block
+  lev_orders<NT, C, true>(reinterpret_cast<const float4*>(c64), a, N, c0, red, sh, rank);
   __syncthreads();
   LevResult r;
   r.status = sh->status;

@@ -44,6 +44,8 @@ __host__ __device__ constexpr int threads_for() { return 256; }
 constexpr int kSmemBytes = 200 * 1024;
 constexpr double kEpsL = 2.220446049250313e-16;
 constexpr int kST_OK = 0, kST_NUMERIC = 4, kST_NOTCONV = 5;
+// blocks per cluster for recursions too large for shared memory
+constexpr int kBigCluster = 8;
 
 // whether the recursion's c and a (2N complex doubles) and the first-column
 // tables fit in the block's dynamic shared memory
@@ -61,11 +63,13 @@ struct FitShared {
   double dred[kNT / 32];
   LevShared lev;
   // cluster mode: the recursion request the first block of a cluster writes
-  // into the second block's copy before the barrier that releases it
-  // (op 1: recursion of order N with c_0; op 0: no more work)
+  // into the other blocks' copies before the barrier that releases them
+  // (op 1: shared-memory recursion of order N with c_0, two blocks; op 2: the
+  // same on the global vectors c, a; op 0: no more work)
   struct alignas(16) {
     int op, N;
     double c0;
+    c128 *c, *a;
   } cmd;
   // instance state (written by thread 0, read by all after a barrier)
   int inst, K, status, n_evals, n_grid, cand_count, flag;
@@ -172,7 +176,7 @@ struct FitArgs {
   char* ws;
   size_t ws_bytes;
   int* counter;
-  int cluster;  // 1: launched as clusters of two blocks (double-float path)
+  int cluster;  // blocks per cluster: 1, 2 (shared-memory recursion) or kBigCluster (global)
 };
 
 __device__ __forceinline__ double prior_term(int K, int N, double zeta) {
@@ -216,7 +220,8 @@ struct Fitter {
     block_first_column<kNT>(lev_c, th, ga, K, beta, N, tables);
     LevResult lr;
     if constexpr (PREC == 2) {
-      if (A->cluster && lev_smem) lr = cluster_levinson();
+      if (A->cluster == 2 && lev_smem) lr = cluster_levinson();
+      else if (A->cluster == kBigCluster && !lev_smem) lr = cluster_levinson_big();
       else lr = block_levinson_df<kNT>(lev_c, lev_a, N, (float4*)sh->red, &sh->lev);
     } else {
       lr = block_levinson<kNT>(lev_c, lev_a, N, sh->red, &sh->lev);
@@ -256,16 +261,43 @@ struct Fitter {
   // hand the request over, run the orders together, and convert a back.
   __device__ LevResult cluster_levinson() {
     const double c0 = lev_prologue<kNT>(lev_c, lev_a, N);
-    if (threadIdx.x == 0) send_cmd(1, N, c0);
+    if (threadIdx.x == 0) send_cmd(1, N, c0, nullptr, nullptr);
     cluster_barrier();
     cluster_levinson_df<kNT>(lev_c, lev_a, N, c0, (float4*)sh->red, &sh->lev);
     return lev_epilogue<kNT>(lev_a, N, &sh->lev);
   }
-  __device__ void send_cmd(int op, int n, double c0) const {
-    const unsigned dst = cluster_addr(&sh->cmd, 1u);
-    const float4 v = make_float4(__int_as_float(op), __int_as_float(n), __int_as_float(__double2loint(c0)),
-                                 __int_as_float(__double2hiint(c0)));
-    st_cluster(dst, v);
+  // A large instance: c and a stay in the workspace (global memory) and all
+  // kBigCluster blocks of the cluster work on them.
+  __device__ LevResult cluster_levinson_big() {
+    const double c0 = lev_prologue<kNT>(lev_c, lev_a, N);
+    if (threadIdx.x == 0) send_cmd(2, N, c0, lev_c, lev_a);
+    cluster_barrier();
+    cluster_levinson_global<kNT, kBigCluster>(lev_c, lev_a, N, c0, (float4*)sh->red, &sh->lev);
+    // the other blocks' entries of a were stored on other SMs: read through L2
+    float4* a4 = reinterpret_cast<float4*>(lev_a);
+    for (int i = threadIdx.x; i < N; i += kNT) {
+      const float4 v = __ldcg(a4 + i);
+      lev_a[i] = mk(to_d(re_of(v)), to_d(im_of(v)));
+    }
+    __syncthreads();
+    LevResult r;
+    r.status = sh->lev.status;
+    r.delta_last = sh->lev.delta;
+    r.logdet = sh->lev.logdet;
+    return r;
+  }
+  // write the request into every other block of the cluster
+  __device__ void send_cmd(int op, int n, double c0, c128* c, c128* a) const {
+    const float4 v0 = make_float4(__int_as_float(op), __int_as_float(n), __int_as_float(__double2loint(c0)),
+                                  __int_as_float(__double2hiint(c0)));
+    const unsigned long long pc = (unsigned long long)c, pa = (unsigned long long)a;
+    const float4 v1 = make_float4(__int_as_float((int)(pc & 0xffffffffu)), __int_as_float((int)(pc >> 32)),
+                                  __int_as_float((int)(pa & 0xffffffffu)), __int_as_float((int)(pa >> 32)));
+    for (int r = 1; r < A->cluster; ++r) {
+      const unsigned dst = cluster_addr(&sh->cmd, (unsigned)r);
+      st_cluster(dst, v0);
+      st_cluster(dst + 16u, v1);
+    }
   }
 
   // The Newton sums keep FP64 accuracy on every path (FP64, or double-float
@@ -774,22 +806,27 @@ struct Fitter {
   }
 };
 
-// The second block of a cluster: it waits for recursion requests from the
-// first block and runs its half of each (double-float path only).
+// The other blocks of a cluster: they wait for recursion requests from the
+// first block and run their share of each (double-float path only).
 template <int kNT>
-__device__ void cluster_helper(FitShared<kNT>& sh, char* dsm) {
+__device__ void cluster_helper(FitShared<kNT>& sh, char* dsm, int csize) {
   for (;;) {
     cluster_barrier();  // a request (or the end) is in sh.cmd
     const int op = sh.cmd.op, n = sh.cmd.N;
     const double c0 = sh.cmd.c0;
-    if (op != 1) break;
-    c128* c = reinterpret_cast<c128*>(dsm);
-    c128* a = c + n;
-    const unsigned src = cluster_addr(c, 0u);
-    float4* c4 = reinterpret_cast<float4*>(c);
-    for (int i = threadIdx.x; i < n; i += kNT) c4[i] = ld_cluster(src + 16u * (unsigned)i);
-    __syncthreads();
-    cluster_levinson_df<kNT>(c, a, n, c0, (float4*)sh.red, &sh.lev);
+    if (op == 1 && csize == 2) {
+      c128* c = reinterpret_cast<c128*>(dsm);
+      c128* a = c + n;
+      const unsigned src = cluster_addr(c, 0u);
+      float4* c4 = reinterpret_cast<float4*>(c);
+      for (int i = threadIdx.x; i < n; i += kNT) c4[i] = ld_cluster(src + 16u * (unsigned)i);
+      __syncthreads();
+      cluster_levinson_df<kNT>(c, a, n, c0, (float4*)sh.red, &sh.lev);
+    } else if (op == 2 && csize == kBigCluster) {
+      cluster_levinson_global<kNT, kBigCluster>(sh.cmd.c, sh.cmd.a, n, c0, (float4*)sh.red, &sh.lev);
+    } else {
+      break;
+    }
   }
 }
 
@@ -803,10 +840,10 @@ __global__ void __launch_bounds__(threads_for<PREC>(), 1) fit_kernel(FitArgs arg
     if (args.cluster) {
       cluster_barrier();  // both blocks running before any shared-memory store between them
       if (cluster_ctarank() != 0) {
-        cluster_helper<threads_for<PREC>()>(sh, dsm);
+        cluster_helper<threads_for<PREC>()>(sh, dsm, args.cluster);
         return;
       }
-      unit = blockIdx.x >> 1;
+      unit = blockIdx.x / args.cluster;
     }
   }
   Fitter<PREC> F;
@@ -826,8 +863,8 @@ __global__ void __launch_bounds__(threads_for<PREC>(), 1) fit_kernel(FitArgs arg
     F.run(b);
   }
   if constexpr (PREC == 2) {
-    if (args.cluster) {  // release the second block
-      if (threadIdx.x == 0) F.send_cmd(0, 0, 0.0);
+    if (args.cluster) {  // release the other blocks
+      if (threadIdx.x == 0) F.send_cmd(0, 0, 0.0, nullptr, nullptr);
       cluster_barrier();
     }
   }
@@ -846,13 +883,13 @@ static cudaError_t launch_prec(const FitArgs& a, int grid, cudaStream_t stream) 
   if (e != cudaSuccess) return e;
   if (a.cluster) {
     cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3(2 * grid);
+    lc.gridDim = dim3(a.cluster * grid);
     lc.blockDim = dim3(threads_for<PREC>());
     lc.dynamicSmemBytes = kSmemBytes;
     lc.stream = stream;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.x = a.cluster;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     lc.attrs = at;
@@ -878,15 +915,22 @@ cudaError_t launch_fit(int prec, const float* y, const InstDesc* inst, int B, in
   a.ws = (char*)ws;
   a.ws_bytes = fit_workspace_bytes(Nmax, Lmax, prec);
   a.counter = counter;
-  // Clusters of two blocks (the second one runs half of every recursion)
-  // when the batch leaves at least one spare SM per instance and the
-  // recursion of every instance runs in shared memory.
+  // Clusters (double-float path): of two blocks, sharing every recursion
+  // through shared memory, when the batch leaves a spare SM per instance and
+  // every instance's recursion fits in shared memory; of kBigCluster blocks,
+  // sharing the recursions of the instances too large for shared memory
+  // through global memory, when the batch leaves kBigCluster SMs per instance.
   a.cluster = 0;
-  if (prec == 2 && cfg.cluster && lev_in_smem(Nmax)) {
+  if (prec == 2 && cfg.cluster) {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && 2 * grid <= sms)
-      a.cluster = 1;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {
+      if (lev_in_smem(Nmax)) {
+        if (2 * grid <= sms) a.cluster = 2;
+      } else if (kBigCluster * grid <= sms) {
+        a.cluster = kBigCluster;
+      }
+    }
   }
   switch (prec) {
     case 0: return launch_prec<0>(a, grid, stream);

@@ -143,3 +143,26 @@ def test_cluster_recursion_matches_one_block():
             assert np.all(wrapdist(a["theta"], b["theta"]) < 1e-9)
             assert np.allclose(a["gamma"], b["gamma"], rtol=1e-8)
         assert abs(a["beta"] - b["beta"]) <= 1e-9 * b["beta"]
+
+
+def test_big_cluster_recursion_matches_one_block():
+    """Double-float path, instances too large for the shared-memory recursion:
+    a small batch runs each recursion on a cluster of eight blocks sharing c
+    and a in global memory; the fits equal the one-block fits to rounding."""
+    from paper_1705_06073_gb300 import build, lse
+    build.build()
+    insts = [synth.make_instance(N, K, 20.0, 8200 + i) for i, (N, K) in enumerate([(8192, 64), (6500, 40)])]
+    res = {}
+    for flags in (0, lse.LSE_FLAG_NO_CLUSTER):
+        ctx = lse.lse_create(lse.lse_config_default(precision=lse.LSE_PREC_MIXED_DF, flags=flags))
+        try:
+            res[flags] = lse.lse_fit_batch(ctx, [i.y for i in insts])
+        finally:
+            lse.lse_destroy(ctx)
+    for a, b in zip(res[0], res[lse.LSE_FLAG_NO_CLUSTER]):
+        assert a["status"] == b["status"] and a["status"] in (0, lse.LSE_ENOTCONV)
+        assert a["K"] == b["K"] and a["n_evals"] == b["n_evals"] and a["iters"] == b["iters"]
+        if a["K"]:
+            assert np.all(wrapdist(a["theta"], b["theta"]) < 1e-9)
+            assert np.allclose(a["gamma"], b["gamma"], rtol=1e-8)
+        assert abs(a["beta"] - b["beta"]) <= 1e-9 * b["beta"]
