@@ -90,12 +90,15 @@ typedef struct lse_config {
 #define LSE_FLAG_NO_AUTOTUNE 1u
 
 /* Run every fit in one block per instance.  By default, on the double-float
- * path (LSE_PREC_MIXED_DF), a fit launch whose instances all have N small
- * enough for the recursion to run in shared memory (N <= about 6000) and that
- * leaves at least one spare SM per instance runs as thread-block clusters of
- * two: the second block of each cluster takes half of every Levinson order.
- * The results agree with the one-block launch to rounding (the inner
- * products are summed in a different order). */
+ * path (LSE_PREC_MIXED_DF), a fit launch runs as thread-block clusters that
+ * share each instance's Levinson recursion: of two blocks when every N is
+ * small enough for the recursion to run in shared memory (N <= about 6000)
+ * and the launch leaves a spare SM per instance (the second block takes half
+ * of every order); of eight blocks, sharing the recursion's vectors in global
+ * memory, when some N is larger and the launch leaves eight SMs per instance
+ * (instances of that launch small enough for shared memory still run in one
+ * block).  The results agree with the one-block launch to rounding (the
+ * inner products are summed in a different order). */
 #define LSE_FLAG_NO_CLUSTER 2u
 
 /* Fill cfg with the paper's defaults (device 0, FP64, tau = 5, ...). */
