@@ -582,7 +582,8 @@ lse_status lse_eval_grid_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* 
   c64* x32 = omega32 + 2 * totN;
   record(ctx, 1, st, true);
   cudaError_t e = launch_factor(ctx->cfg.precision == LSE_PREC_MIXED_DF, y_d, (const InstDesc*)ctx->desc.p, B, Nmax, theta_d, gamma_d, beta_d, tables(ctx),
-                                ctx->ws.p, rho, x, omega, omega32, x32, delta, status, st);
+                                ctx->ws.p, rho, x, omega, omega32, x32, delta, status,
+                                !(ctx->cfg.flags & LSE_FLAG_NO_CLUSTER), st);
   record(ctx, 1, st, false);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "factor kernel launch");
   // the grid kernel reuses the workspace; its offset table goes first

@@ -479,6 +479,29 @@ __device__ __noinline__ LevResult cluster_levinson_df(const c128* c64, c128* a64
   return r;
 }
 
+// A recursion request from the first block of a cluster to the others
+// (op 1: shared-memory recursion of order N with c_0, two blocks; op 2: the
+// same on the global vectors c, a; op 0: no more work).
+struct alignas(16) LevCmd {
+  int op, N;
+  double c0;
+  c128 *c, *a;
+};
+
+// write `v` into the LevCmd at the same shared address in blocks 1..csize-1
+__device__ __forceinline__ void lev_send_cmd(const LevCmd* local, int csize, const LevCmd& v) {
+  const float4 v0 = make_float4(__int_as_float(v.op), __int_as_float(v.N), __int_as_float(__double2loint(v.c0)),
+                                __int_as_float(__double2hiint(v.c0)));
+  const unsigned long long pc = (unsigned long long)v.c, pa = (unsigned long long)v.a;
+  const float4 v1 = make_float4(__int_as_float((int)(pc & 0xffffffffu)), __int_as_float((int)(pc >> 32)),
+                                __int_as_float((int)(pa & 0xffffffffu)), __int_as_float((int)(pa >> 32)));
+  for (int r = 1; r < csize; ++r) {
+    const unsigned dst = cluster_addr(local, (unsigned)r);
+    st_cluster(dst, v0);
+    st_cluster(dst + 16u, v1);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // The recursion of a large instance shared by the C blocks of a cluster, with
 // c and a in global memory (the instance's workspace; L2-resident), called by

@@ -62,15 +62,7 @@ struct FitShared {
   MinLoc ml[kNT / 32];
   double dred[kNT / 32];
   LevShared lev;
-  // cluster mode: the recursion request the first block of a cluster writes
-  // into the other blocks' copies before the barrier that releases them
-  // (op 1: shared-memory recursion of order N with c_0, two blocks; op 2: the
-  // same on the global vectors c, a; op 0: no more work)
-  struct alignas(16) {
-    int op, N;
-    double c0;
-    c128 *c, *a;
-  } cmd;
+  LevCmd cmd;  // cluster mode: request from the first block (lev_send_cmd)
   // instance state (written by thread 0, read by all after a barrier)
   int inst, K, status, n_evals, n_grid, cand_count, flag;
   double beta, zeta, eps_beta, tau;
@@ -288,16 +280,7 @@ struct Fitter {
   }
   // write the request into every other block of the cluster
   __device__ void send_cmd(int op, int n, double c0, c128* c, c128* a) const {
-    const float4 v0 = make_float4(__int_as_float(op), __int_as_float(n), __int_as_float(__double2loint(c0)),
-                                  __int_as_float(__double2hiint(c0)));
-    const unsigned long long pc = (unsigned long long)c, pa = (unsigned long long)a;
-    const float4 v1 = make_float4(__int_as_float((int)(pc & 0xffffffffu)), __int_as_float((int)(pc >> 32)),
-                                  __int_as_float((int)(pa & 0xffffffffu)), __int_as_float((int)(pa >> 32)));
-    for (int r = 1; r < A->cluster; ++r) {
-      const unsigned dst = cluster_addr(&sh->cmd, (unsigned)r);
-      st_cluster(dst, v0);
-      st_cluster(dst + 16u, v1);
-    }
+    lev_send_cmd(&sh->cmd, A->cluster, LevCmd{op, n, c0, c, a});
   }
 
   // The Newton sums keep FP64 accuracy on every path (FP64, or double-float

@@ -47,16 +47,34 @@ __host__ __device__ inline FactorLayout factor_layout(int Nmax) {
   return L;
 }
 
+// blocks per cluster for large-N recursions of the double-float factor kernel
+constexpr int kFactorCluster = 8;
+
+// csize > 1 (double-float only): clusters of csize blocks, one instance per
+// cluster; the first block does everything and the others join the Levinson
+// recursion of an instance too large for shared memory (or are released).
 template <bool DF>
 __global__ void __launch_bounds__(factor_threads<DF>(), 1)
     factor_kernel(const float* y, const InstDesc* inst, int Nmax, const double* theta, const double* gamma,
                   const double* beta, Tables tab, char* ws, size_t ws_bytes, c128* rho_out, c128* x_out,
-                  c128* omega_out, c64* omega32_out, c64* x32_out, double* delta_out, int* status) {
+                  c128* omega_out, c64* omega32_out, c64* x32_out, double* delta_out, int* status, int csize) {
   constexpr int kFNT = factor_threads<DF>();
   __shared__ c128 red[kFNT];
   __shared__ LevShared lev;
+  __shared__ LevCmd cmd;
   extern __shared__ __align__(16) char dsm[];
-  const int b = blockIdx.x;
+  int b = blockIdx.x;
+  if constexpr (DF) {
+    if (csize > 1) {
+      cluster_barrier();  // every block running before any store between them
+      if (cluster_ctarank() != 0) {
+        cluster_barrier();  // the request (or the release) is in cmd
+        if (cmd.op == 2) cluster_levinson_global<kFNT, kFactorCluster>(cmd.c, cmd.a, cmd.N, cmd.c0, (float4*)red, &lev);
+        return;
+      }
+      b = blockIdx.x / csize;
+    }
+  }
   const InstDesc d = inst[b];
   const int N = d.N;
   char* base = ws + (size_t)b * ws_bytes;
@@ -83,8 +101,34 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
   }
   block_first_column<kFNT>(cc, theta + d.k_off, gamma + d.k_off, d.K, beta[b], N, tables);
   LevResult lr;
-  if constexpr (DF) lr = block_levinson_df<kFNT>(cc, aa, N, (float4*)red, &lev);
-  else lr = block_levinson<kFNT>(cc, aa, N, red, &lev);
+  if constexpr (DF) {
+    if (csize > 1) {
+      // exactly one request per launch: the shared recursion, or a release
+      const bool big = cc != (c128*)dsm;
+      double c0 = 0.0;
+      if (big) c0 = lev_prologue<kFNT>(cc, aa, N);
+      if (threadIdx.x == 0) lev_send_cmd(&cmd, csize, LevCmd{big ? 2 : 0, N, c0, cc, aa});
+      cluster_barrier();
+      if (big) {
+        cluster_levinson_global<kFNT, kFactorCluster>(cc, aa, N, c0, (float4*)red, &lev);
+        float4* a4 = reinterpret_cast<float4*>(aa);
+        for (int i = threadIdx.x; i < N; i += kFNT) {  // other SMs stored parts of a: read through L2
+          const float4 v = __ldcg(a4 + i);
+          aa[i] = mk(to_d(re_of(v)), to_d(im_of(v)));
+        }
+        __syncthreads();
+        lr.status = lev.status;
+        lr.delta_last = lev.delta;
+        lr.logdet = lev.logdet;
+      } else {
+        lr = block_levinson_df<kFNT>(cc, aa, N, (float4*)red, &lev);
+      }
+    } else {
+      lr = block_levinson_df<kFNT>(cc, aa, N, (float4*)red, &lev);
+    }
+  } else {
+    lr = block_levinson<kFNT>(cc, aa, N, red, &lev);
+  }
   c128* rho = rho_out + d.y_off;
   c128* x = x_out + d.y_off;
   if (lr.status) {
@@ -281,24 +325,53 @@ template <bool DF>
 static cudaError_t launch_factor_t(const float* y, const InstDesc* inst, int B, int Nmax, const double* theta,
                                    const double* gamma, const double* beta, const Tables& tab, void* ws,
                                    c128* rho_out, c128* x_out, c128* omega_out, c64* omega32_out, c64* x32_out,
-                                   double* delta_out, int* status, cudaStream_t stream) {
+                                   double* delta_out, int* status, bool allow_cluster, cudaStream_t stream) {
   const int smem = 200 * 1024;
   cudaError_t e = cudaFuncSetAttribute(factor_kernel<DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  factor_kernel<DF><<<B, factor_threads<DF>(), smem, stream>>>(y, inst, Nmax, theta, gamma, beta, tab, (char*)ws,
-                                               factor_workspace_bytes(Nmax), rho_out, x_out, omega_out,
-                                               omega32_out, x32_out, delta_out, status);
+  // clusters of kFactorCluster blocks (double-float) when some recursion is
+  // too large for shared memory and the launch leaves the SMs for them
+  int csize = 1;
+  if (DF && allow_cluster) {
+    int S, H;
+    first_column_split(Nmax, S, H);
+    const size_t need = 2 * sizeof(c128) * (size_t)Nmax + sizeof(c128) * kFirstColumnChunk * (S + H);
+    int dev = 0, sms = 0;
+    if (need > (size_t)smem && cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && kFactorCluster * B <= sms)
+      csize = kFactorCluster;
+  }
+  const size_t wsb = factor_workspace_bytes(Nmax);
+  if (csize > 1) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(csize * B);
+    lc.blockDim = dim3(factor_threads<DF>());
+    lc.dynamicSmemBytes = smem;
+    lc.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, factor_kernel<DF>, y, inst, Nmax, theta, gamma, beta, tab, (char*)ws, wsb, rho_out,
+                              x_out, omega_out, omega32_out, x32_out, delta_out, status, csize);
+  }
+  factor_kernel<DF><<<B, factor_threads<DF>(), smem, stream>>>(y, inst, Nmax, theta, gamma, beta, tab, (char*)ws, wsb,
+                                                               rho_out, x_out, omega_out, omega32_out, x32_out,
+                                                               delta_out, status, 1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_factor(bool df, const float* y, const InstDesc* inst, int B, int Nmax, const double* theta,
                           const double* gamma, const double* beta, const Tables& tab, void* ws, c128* rho_out,
                           c128* x_out, c128* omega_out, c64* omega32_out, c64* x32_out, double* delta_out,
-                          int* status, cudaStream_t stream) {
+                          int* status, bool allow_cluster, cudaStream_t stream) {
   return df ? launch_factor_t<true>(y, inst, B, Nmax, theta, gamma, beta, tab, ws, rho_out, x_out, omega_out,
-                                    omega32_out, x32_out, delta_out, status, stream)
+                                    omega32_out, x32_out, delta_out, status, allow_cluster, stream)
             : launch_factor_t<false>(y, inst, B, Nmax, theta, gamma, beta, tab, ws, rho_out, x_out, omega_out,
-                                     omega32_out, x32_out, delta_out, status, stream);
+                                     omega32_out, x32_out, delta_out, status, false, stream);
 }
 
 size_t grid_workspace_bytes(int B, int64_t total_L, bool f32) {

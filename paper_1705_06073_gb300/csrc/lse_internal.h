@@ -66,7 +66,7 @@ size_t factor_workspace_bytes(int Nmax);
 cudaError_t launch_factor(bool df, const float* y, const InstDesc* inst, int B, int Nmax, const double* theta,
                           const double* gamma, const double* beta, const Tables& tab, void* ws, c128* rho_out,
                           c128* x_out, c128* omega_out, c64* omega32_out, c64* x32_out, double* delta_out,
-                          int* status, cudaStream_t stream);
+                          int* status, bool allow_cluster, cudaStream_t stream);
 // Eval-grid: spectra and combine.  outputs in T (float for mixed, double for fp64).
 // Schedule of the on-chip grid FFT kernel.
 struct GridVariant {
