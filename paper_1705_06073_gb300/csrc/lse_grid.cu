@@ -51,8 +51,9 @@ __host__ __device__ inline FactorLayout factor_layout(int Nmax) {
 constexpr int kFactorCluster = 8;
 
 // csize > 1 (double-float only): clusters of csize blocks, one instance per
-// cluster; the first block does everything and the others join the Levinson
-// recursion of an instance too large for shared memory (or are released).
+// cluster; the first block does everything and the others join its Levinson
+// recursion (csize 2: shared-memory copies; kFactorCluster: global memory,
+// for an instance too large for shared memory), or are released.
 template <bool DF>
 __global__ void __launch_bounds__(factor_threads<DF>(), 1)
     factor_kernel(const float* y, const InstDesc* inst, int Nmax, const double* theta, const double* gamma,
@@ -69,7 +70,18 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
       cluster_barrier();  // every block running before any store between them
       if (cluster_ctarank() != 0) {
         cluster_barrier();  // the request (or the release) is in cmd
-        if (cmd.op == 2) cluster_levinson_global<kFNT, kFactorCluster>(cmd.c, cmd.a, cmd.N, cmd.c0, (float4*)red, &lev);
+        if (cmd.op == 1 && csize == 2) {
+          // shared-memory recursion: copy the first block's double-float column
+          const int n = cmd.N;
+          c128* c = reinterpret_cast<c128*>(dsm);
+          const unsigned src = cluster_addr(c, 0u);
+          float4* c4 = reinterpret_cast<float4*>(c);
+          for (int i = threadIdx.x; i < n; i += kFNT) c4[i] = ld_cluster(src + 16u * (unsigned)i);
+          __syncthreads();
+          cluster_levinson_df<kFNT>(c, c + n, n, cmd.c0, (float4*)red, &lev);
+        } else if (cmd.op == 2 && csize == kFactorCluster) {
+          cluster_levinson_global<kFNT, kFactorCluster>(cmd.c, cmd.a, cmd.N, cmd.c0, (float4*)red, &lev);
+        }
         return;
       }
       b = blockIdx.x / csize;
@@ -104,12 +116,16 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
   if constexpr (DF) {
     if (csize > 1) {
       // exactly one request per launch: the shared recursion, or a release
-      const bool big = cc != (c128*)dsm;
+      const bool in_smem = cc == (c128*)dsm;
+      const int op = (csize == 2 && in_smem) ? 1 : (csize == kFactorCluster && !in_smem) ? 2 : 0;
       double c0 = 0.0;
-      if (big) c0 = lev_prologue<kFNT>(cc, aa, N);
-      if (threadIdx.x == 0) lev_send_cmd(&cmd, csize, LevCmd{big ? 2 : 0, N, c0, cc, aa});
+      if (op) c0 = lev_prologue<kFNT>(cc, aa, N);
+      if (threadIdx.x == 0) lev_send_cmd(&cmd, csize, LevCmd{op, N, c0, cc, aa});
       cluster_barrier();
-      if (big) {
+      if (op == 1) {
+        cluster_levinson_df<kFNT>(cc, aa, N, c0, (float4*)red, &lev);
+        lr = lev_epilogue<kFNT>(aa, N, &lev);
+      } else if (op == 2) {
         cluster_levinson_global<kFNT, kFactorCluster>(cc, aa, N, c0, (float4*)red, &lev);
         float4* a4 = reinterpret_cast<float4*>(aa);
         for (int i = threadIdx.x; i < N; i += kFNT) {  // other SMs stored parts of a: read through L2
@@ -329,17 +345,24 @@ static cudaError_t launch_factor_t(const float* y, const InstDesc* inst, int B, 
   const int smem = 200 * 1024;
   cudaError_t e = cudaFuncSetAttribute(factor_kernel<DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  // clusters of kFactorCluster blocks (double-float) when some recursion is
-  // too large for shared memory and the launch leaves the SMs for them
+  // clusters (double-float): of two blocks when every recursion runs in
+  // shared memory and the launch leaves a spare SM per instance; of
+  // kFactorCluster blocks when some recursion is too large for shared memory
+  // and the launch leaves the SMs for them
   int csize = 1;
   if (DF && allow_cluster) {
     int S, H;
     first_column_split(Nmax, S, H);
     const size_t need = 2 * sizeof(c128) * (size_t)Nmax + sizeof(c128) * kFirstColumnChunk * (S + H);
     int dev = 0, sms = 0;
-    if (need > (size_t)smem && cudaGetDevice(&dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && kFactorCluster * B <= sms)
-      csize = kFactorCluster;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {
+      if (need <= (size_t)smem) {
+        if (2 * B <= sms) csize = 2;
+      } else if (kFactorCluster * B <= sms) {
+        csize = kFactorCluster;
+      }
+    }
   }
   const size_t wsb = factor_workspace_bytes(Nmax);
   if (csize > 1) {
