@@ -186,6 +186,7 @@ def oracle_sample(threads: int, frac: float = 1 / 16):
     per_fit = r["n_evals"] * r["t_eval"] + r["n_grid"] * r["t_grid"]
     r["value"] = 1.0 / per_fit
     r["wall"] = wall
+    r["frac"] = frac
     return r
 
 
@@ -193,7 +194,7 @@ def cpu_desc(r, threads):
     return {"value": r["value"], "unit": "fitted instances/s", "cores": threads, "kind": "oracle",
             "sample": (f"dense FP64 oracle on one instance of the workload (N={N}, K={K}): one full "
                        f"evaluation (Cholesky, ln|C|, C^-1 y, eqs. q-x) took {r['t_eval']:.3f} s and one "
-                       f"{L}-point grid evaluation {r['t_grid']:.3f} s (timed on 1/16 of the points, "
+                       f"{L}-point grid evaluation {r['t_grid']:.3f} s (timed on 1/{round(1 / r.get('frac', 1 / 16))} of the points, "
                        f"scaled); per-fit cost = {r['n_evals']:.1f} evaluations + {r['n_grid']:.1f} grid "
                        f"evaluations, the counts of the oracle's own complete fits of the same generator "
                        f"at N=512, K=8 (same K/N)")}
@@ -202,6 +203,7 @@ def cpu_desc(r, threads):
 def run_reference(args, rank):
     if rank != 0:
         return
+    Bn = args.batch
     threads = os.cpu_count() or 1
     vals = []
     for i in range(args.warmup + args.steps):
@@ -215,7 +217,8 @@ def run_reference(args, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "fitted instances/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median([x["wall"] for x in vals]),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD if Bn == B else f"batch{Bn}_n4096_k64_l16384", "B": Bn, "N": N, "K": K, "L": L, "l2": "n/a (CPU)"},
+            "config": {"workload": WORKLOAD if Bn == B else f"batch{Bn}_n4096_k64_l16384", "B": Bn, "N": N, "K": K, "L": L,
+                       "snr_db": "U[10,30]", "l2": "n/a (CPU)", "parallelism": "oracle on the host cores"},
             "cpu_baseline": desc,
             "e2e": {"value": v, "unit": "fitted instances/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
