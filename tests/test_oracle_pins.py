@@ -233,6 +233,33 @@ def test_delta_objective_is_the_objective_change():
         assert abs(dl[i] - ref) < 1e-9 * max(1, abs(ref))
 
 
+def test_activation_criterion_is_the_sign_of_the_objective_change():
+    """Eq. (activate_derived) rearranges Delta L < 0 of eq. (delta_L): with the
+    dense objective change as the reference, the criterion with tau = 0 holds
+    exactly where activating lowers the objective; tau shifts the threshold
+    of |q|^2 / s (eq. activate_criterion)."""
+    N = 24
+    y, th, g, b = rand_state(N, 2, 43)
+    ev = dn.DenseEval(y, th, g, b)
+    pts = np.linspace(0.0, 1.0, 41, endpoint=False)
+    gr = ev.grid(0, points=pts)
+    checked, outcomes = 0, set()
+    for zeta in (0.05, 0.2, 0.45):
+        for gbar in (0.3, 2.0, 9.0):
+            ok = dn.activation_test(gr["q"], gr["s"], gbar, zeta, 0.0)
+            for i, t in enumerate(pts):
+                ev2 = dn.DenseEval(y, np.append(th, t), np.append(g, gbar), b)
+                d = ev2.objective(zeta) - ev.objective(zeta)
+                if abs(d) > 1e-9:  # away from the boundary
+                    assert bool(ok[i]) == (d < 0.0), (zeta, gbar, t, d)
+                    checked += 1
+                    outcomes.add(bool(ok[i]))
+            ratio = np.abs(gr["q"]) ** 2 / gr["s"]
+            rhs = dn.activation_rhs(gr["s"], gbar, zeta)
+            assert np.array_equal(dn.activation_test(gr["q"], gr["s"], gbar, zeta, 5.0), ratio > rhs + 5.0)
+    assert checked > 300 and outcomes == {True, False}
+
+
 def test_activate_gamma_minimises_objective():
     from scipy.optimize import minimize_scalar
     N = 30
