@@ -209,8 +209,10 @@ LSE_API void lse_plan_destroy(lse_plan* plan);
  * the remaining device-memory budget cfg->hbm_budget_bytes allows; 0 = no
  * cap) and launch one batched fit over them.  Requests that arrive while
  * other groups run start on free slots, so their work overlaps on the
- * device.  Each instance is fitted by one thread block with the arithmetic of
- * a lone lse_fit, so its result does not depend on the batch it ran in.
+ * device.  Each instance is fitted with the arithmetic of a lone lse_fit, so
+ * its result does not depend on the batch it ran in: bit for bit when the
+ * group and the lone fit run in the same unit mode (one block, or a cluster;
+ * see LSE_FLAG_NO_CLUSTER), to rounding otherwise.
  * Not thread-safe: one server per host thread. */
 typedef struct lse_server lse_server;
 

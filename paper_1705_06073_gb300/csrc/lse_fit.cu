@@ -4,7 +4,9 @@
 // pulling instances from a device work counter, with every model evaluation
 // done by the superfast route of Sec. III (Levinson recursion for the
 // Gohberg-Semencul generators, FFT convolutions, FFT grid, direct off-grid
-// sums).
+// sums).  On the double-float path a small batch runs as thread-block
+// clusters: the first block of each cluster runs the estimator and the other
+// blocks only take their share of every Levinson recursion.
 //
 // Readings of the paper (the same ones the CPU oracle follows):
 //  - (theta, gamma) update: one per-component diagonal Newton step with the

@@ -4,9 +4,10 @@
 // theta-derivatives at theta_l = l/L.
 //
 // Two kernels:
-//  factor_kernel  one block per instance: first column of C, Levinson
-//                 recursion (Gohberg-Semencul generators rho, delta) and
-//                 x = C^{-1} y by FFT convolutions (Sec. III-A, III-B).
+//  factor_kernel  one block (or, double-float, one thread-block cluster) per
+//                 instance: first column of C, Levinson recursion
+//                 (Gohberg-Semencul generators rho, delta) and x = C^{-1} y
+//                 by FFT convolutions (Sec. III-A, III-B).
 //  grid_kernel    the length-L spectra of index-weighted generators and the
 //                 pointwise combine.  With c = (N-2)/2 and
 //                   Q_a = DFT_L((n-c)^a rho_n),  X_a = DFT_L(n^a x_n)

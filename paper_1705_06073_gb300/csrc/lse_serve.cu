@@ -74,7 +74,7 @@ struct lse_server {
 
 namespace {
 
-// device memory a group needs on a slot: fit workspace (one block per
+// device memory a group needs on a slot: fit workspace (one unit per
 // instance up to the SM count) plus the input and output buffers
 uint64_t group_bytes(const lse_server* s, const std::vector<Request>& g) {
   int Nmax = 0, Lmax = 0;
