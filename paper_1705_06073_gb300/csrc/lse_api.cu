@@ -38,6 +38,7 @@ struct lse_ctx {
   // twiddle tables exp(-j 2 pi k / 2^log2max)
   c128* tw64 = nullptr;
   c64* tw32 = nullptr;
+  float4* twdf = nullptr;
   int log2max = 0;
   DevBuf ws, desc, counter, stage_in, stage_out, fac, tasks;
   size_t allocated = 0;
@@ -100,13 +101,15 @@ lse_status ensure(lse_ctx* c, DevBuf& b, size_t bytes) {
   return LSE_OK;
 }
 
-__global__ void twiddle_kernel(c128* t64, c64* t32, int log2m) {
+__global__ void twiddle_kernel(c128* t64, c64* t32, float4* tdf, int log2m) {
   const int M = 1 << log2m;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
     double s, c;
     sincospi(2.0 * (double)k / (double)M, &s, &c);
     t64[k] = mk(c, -s);
     t32[k] = mk((float)c, (float)-s);
+    const float ch = (float)c, sh = (float)-s;
+    tdf[k] = make_float4(ch, (float)(c - (double)ch), sh, (float)(-s - (double)sh));
   }
 }
 
@@ -117,19 +120,22 @@ lse_status ensure_tables(lse_ctx* c, int log2m) {
     cudaStreamSynchronize(c->stream);
     cudaFree(c->tw64);
     cudaFree(c->tw32);
+    cudaFree(c->twdf);
     c->tw64 = nullptr;
     c->tw32 = nullptr;
+    c->twdf = nullptr;
   }
   const size_t M = size_t(1) << log2m;
   LSE_CUDA(c, cudaMalloc(&c->tw64, M * sizeof(c128)));
   LSE_CUDA(c, cudaMalloc(&c->tw32, M * sizeof(c64)));
-  twiddle_kernel<<<256, 256, 0, c->stream>>>(c->tw64, c->tw32, log2m);
+  LSE_CUDA(c, cudaMalloc(&c->twdf, M * sizeof(float4)));
+  twiddle_kernel<<<256, 256, 0, c->stream>>>(c->tw64, c->tw32, c->twdf, log2m);
   LSE_CUDA(c, cudaGetLastError());
   c->log2max = log2m;
   return LSE_OK;
 }
 
-Tables tables(const lse_ctx* c) { return Tables{c->tw64, c->tw32, c->log2max}; }
+Tables tables(const lse_ctx* c) { return Tables{c->tw64, c->tw32, c->log2max, c->twdf}; }
 
 int default_L(int N) {
   // 8N rounded to the nearest power of two (Sec. II-C5 footnote)
@@ -294,6 +300,7 @@ void lse_destroy(lse_ctx* ctx) {
     if (b->p) cudaFree(b->p);
   if (ctx->tw64) cudaFree(ctx->tw64);
   if (ctx->tw32) cudaFree(ctx->tw32);
+  if (ctx->twdf) cudaFree(ctx->twdf);
   if (ctx->h_desc) cudaFreeHost(ctx->h_desc);
   for (auto& v : ctx->timed)
     for (auto& t : v) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }

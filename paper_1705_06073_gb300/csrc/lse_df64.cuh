@@ -528,6 +528,144 @@ __device__ __noinline__ LevResult cluster_levinson_global(const c128* c64, c128*
 }
 
 // ---------------------------------------------------------------------------
+// Double-float FFT and Gohberg-Semencul apply (the double-float fit path).
+// Complex double-float values are float4 {re.h, re.l, im.h, im.l}.  Sums use
+// the "sloppy" double-float addition (TwoSum of the heads, the tails added,
+// Fast2Sum renormalisation), whose error is relative to the operands'
+// magnitudes, the usual FFT error model; products keep the cross terms.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ f2 add_s(f2 a, f2 b) {
+  const f2 s = two_sum(a.h, b.h);
+  return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ f2 sub_s(f2 a, f2 b) { return add_s(a, neg(b)); }
+__device__ __forceinline__ f2 mul_f(f2 a, f2 b) {
+  float p, e;
+  prod_terms(a, b, p, e);
+  return fast_two_sum(p, e);
+}
+
+struct cf2 {
+  f2 re, im;
+};
+__device__ __forceinline__ cf2 ld_cf2(float4 v) { return cf2{f2{v.x, v.y}, f2{v.z, v.w}}; }
+__device__ __forceinline__ float4 st_cf2(cf2 a) { return make_float4(a.re.h, a.re.l, a.im.h, a.im.l); }
+__device__ __forceinline__ cf2 cf2_of(c128 v) { return cf2{to_f2(v.re), to_f2(v.im)}; }
+__device__ __forceinline__ cf2 operator+(cf2 a, cf2 b) { return cf2{add_s(a.re, b.re), add_s(a.im, b.im)}; }
+__device__ __forceinline__ cf2 operator-(cf2 a, cf2 b) { return cf2{sub_s(a.re, b.re), sub_s(a.im, b.im)}; }
+__device__ __forceinline__ cf2 operator*(cf2 a, cf2 b) {
+  return cf2{sub_s(mul_f(a.re, b.re), mul_f(a.im, b.im)), add_s(mul_f(a.re, b.im), mul_f(a.im, b.re))};
+}
+__device__ __forceinline__ cf2 conj(cf2 a) { return cf2{a.re, neg(a.im)}; }
+__device__ __forceinline__ cf2 mul_j(cf2 a) { return cf2{neg(a.im), a.re}; }
+// multiplication by a power of two (exact)
+__device__ __forceinline__ cf2 scale2(float s, cf2 a) {
+  return cf2{f2{a.re.h * s, a.re.l * s}, f2{a.im.h * s, a.im.l * s}};
+}
+__device__ __forceinline__ cf2 cf2_zero() { return cf2{f2{0.f, 0.f}, f2{0.f, 0.f}}; }
+
+// exp(-j 2 pi k / M), 0 <= k < M, from the double-float table of 2^log2max points
+struct TwiddlesDF {
+  const float4* tw;
+  int log2max;
+  __device__ __forceinline__ cf2 w(int k, int log2M) const { return ld_cf2(tw[(size_t)k << (log2max - log2M)]); }
+};
+
+// block_fft (Stockham radix-4, decimation in frequency; first level reads
+// gen(i), levels alternate between tmp and dst) in double-float
+template <int NT, class Gen>
+__device__ void block_fft_df(Gen gen, float4* dst, float4* tmp, int log2M, bool inverse, const TwiddlesDF& tw) {
+  const int M = 1 << log2M;
+  const int npass = (log2M >> 1) + (log2M & 1);
+  int pass = 0;
+  const float4* in = nullptr;
+  int n = M, s = 1, log2s = 0;
+  while (n >= 4) {
+    ++pass;
+    float4* out = ((npass - pass) & 1) ? tmp : dst;
+    const int n4 = n >> 2;
+    for (int t = threadIdx.x; t < (M >> 2); t += NT) {
+      const int p = t >> log2s, q = t & (s - 1);
+      cf2 a, b, c, d;
+      if (pass == 1) {
+        a = gen(q + s * p); b = gen(q + s * (p + n4)); c = gen(q + s * (p + 2 * n4)); d = gen(q + s * (p + 3 * n4));
+      } else {
+        a = ld_cf2(in[q + s * p]); b = ld_cf2(in[q + s * (p + n4)]);
+        c = ld_cf2(in[q + s * (p + 2 * n4)]); d = ld_cf2(in[q + s * (p + 3 * n4)]);
+      }
+      const cf2 apc = a + c, amc = a - c, bpd = b + d, jbmd = mul_j(b - d);
+      const cf2 y1 = inverse ? amc + jbmd : amc - jbmd;
+      const cf2 y3 = inverse ? amc - jbmd : amc + jbmd;
+      const cf2 y2 = apc - bpd;
+      cf2 w1 = tw.w(p * s, log2M), w2 = tw.w(2 * p * s, log2M), w3 = tw.w(3 * p * s, log2M);
+      if (inverse) { w1 = conj(w1); w2 = conj(w2); w3 = conj(w3); }
+      out[q + s * (4 * p + 0)] = st_cf2(apc + bpd);
+      out[q + s * (4 * p + 1)] = st_cf2(w1 * y1);
+      out[q + s * (4 * p + 2)] = st_cf2(w2 * y2);
+      out[q + s * (4 * p + 3)] = st_cf2(w3 * y3);
+    }
+    __syncthreads();
+    in = out;
+    n >>= 2; s <<= 2; log2s += 2;
+  }
+  if (n == 2) {
+    ++pass;
+    for (int q = threadIdx.x; q < (M >> 1); q += NT) {
+      cf2 a, b;
+      if (pass == 1) { a = gen(q); b = gen(q + s); } else { a = ld_cf2(in[q]); b = ld_cf2(in[q + s]); }
+      dst[q] = st_cf2(a + b);
+      dst[q + s] = st_cf2(a - b);
+    }
+    __syncthreads();
+  }
+}
+
+// block_gs_apply in double-float: x = C^{-1} y by the Gohberg-Semencul
+// formula (eq. gohberg-semencul) as FFT convolutions, the same six
+// transforms of length M2; rho, Yf = FFT_M2(y) and x in FP64.
+// bufs: 5 arrays of M2 complex (16 bytes each, used as double-float).
+template <int NT>
+__device__ void block_gs_apply_df(const c128* rho, const c128* Yf, c128* x, int N, int log2M2, double delta_last,
+                                  c128* const* bufs, const TwiddlesDF& tw) {
+  const int M2 = 1 << log2M2;
+  const int msk = M2 - 1;
+  const float inv = 1.0f / (float)M2;  // a power of two: exact
+  float4* P = reinterpret_cast<float4*>(bufs[0]);
+  float4* B1 = reinterpret_cast<float4*>(bufs[1]);
+  float4* B2 = reinterpret_cast<float4*>(bufs[2]);
+  float4* B3 = reinterpret_cast<float4*>(bufs[3]);
+  float4* T = reinterpret_cast<float4*>(bufs[4]);
+  block_fft_df<NT>([=] __device__(int i) { return i < N ? cf2_of(rho[i]) : cf2_zero(); }, P, T, log2M2, false, tw);
+  // u = T1 y
+  block_fft_df<NT>(
+      [=] __device__(int w) {
+        return cf2_of(Yf[w]) * conj(tw.w((int)(((int64_t)(N - 1) * w) & msk), log2M2)) * ld_cf2(P[w]);
+      },
+      B1, T, log2M2, true, tw);
+  block_fft_df<NT>([=] __device__(int i) { return i < N ? scale2(inv, ld_cf2(B1[i])) : cf2_zero(); }, B2, T, log2M2,
+                   false, tw);
+  // z = T0^H y
+  block_fft_df<NT>([=] __device__(int w) { return cf2_of(Yf[w]) * conj(tw.w(w, log2M2)) * conj(ld_cf2(P[w])); }, B1,
+                   T, log2M2, true, tw);
+  block_fft_df<NT>([=] __device__(int i) { return i < N ? scale2(inv, ld_cf2(B1[i])) : cf2_zero(); }, B3, T, log2M2,
+                   false, tw);
+  // x = (T1^H u - T0 z) / delta
+  block_fft_df<NT>(
+      [=] __device__(int w) {
+        const cf2 g1 = tw.w((int)(((int64_t)(N - 1) * w) & msk), log2M2) * conj(ld_cf2(P[w]));
+        const cf2 g0 = tw.w(w, log2M2) * ld_cf2(P[w]);
+        return g1 * ld_cf2(B2[w]) - g0 * ld_cf2(B3[w]);
+      },
+      B1, T, log2M2, true, tw);
+  const double sc = (double)inv / delta_last;
+  for (int i = threadIdx.x; i < N; i += NT) {
+    const cf2 v = ld_cf2(B1[i]);
+    x[i] = mk(sc * to_d(v.re), sc * to_d(v.im));
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
 // Off-grid sums of block_active_sums (R_0..R_3 from rho, X_0..X_2 from x with
 // the centred weights (n - c)^a, phases e^{-j2pi n theta_k}) in double-float
 // on the FP32 pipes.  rho_df, x_df: the FP64 vectors converted once per

@@ -228,7 +228,15 @@ struct Fitter {
     for (int n = threadIdx.x; n < N; n += kNT) w.rho[n] = conj(lev_a[N - 1 - n]);
     __syncthreads();
     c128* bufs[5] = {w.buf[0], w.buf[1], w.buf[2], w.buf[3], w.buf[4]};
-    block_gs_apply<kNT>(w.rho, w.Yf, w.x, N, log2M2, lr.delta_last, bufs, tw64);
+    bool gs_done = false;
+    if constexpr (PREC == 2) {  // double-float transforms when the table exists
+      if (A->tab.twdf) {
+        block_gs_apply_df<kNT>(w.rho, w.Yf, w.x, N, log2M2, lr.delta_last, bufs,
+                               TwiddlesDF{A->tab.twdf, A->tab.log2max});
+        gs_done = true;
+      }
+    }
+    if (!gs_done) block_gs_apply<kNT>(w.rho, w.Yf, w.x, N, log2M2, lr.delta_last, bufs, tw64);
     double part = 0.0;
     for (int n = threadIdx.x; n < N; n += kNT) part += (conj(w.y[n]) * w.x[n]).re;
     const double yCy = block_sum<kNT>(part, sh->dred);

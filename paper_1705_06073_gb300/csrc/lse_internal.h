@@ -49,6 +49,9 @@ struct Tables {
   const c128* tw64;
   const c64* tw32;
   int log2max;
+  // the same table as double-float pairs {re.h, re.l, im.h, im.l}, or null
+  // (then the double-float fit path applies the Gohberg-Semencul formula in FP64)
+  const float4* twdf;
 };
 
 // Per-CTA workspace needed by the fit kernel for instances up to (Nmax, Lmax).
