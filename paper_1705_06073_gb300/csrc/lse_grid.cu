@@ -156,7 +156,12 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
   for (int n = threadIdx.x; n < N; n += kFNT) rho[n] = conj(aa[N - 1 - n]);
   block_fft<kFNT, double>([=] __device__(int i) { return i < N ? yv[i] : zero<double>(); }, Yf, bufs[4], log2M2, false,
                           tw);
-  block_gs_apply<kFNT>(rho, Yf, x, N, log2M2, lr.delta_last, bufs, tw);
+  // double-float transforms (Gohberg-Semencul apply and the omega_s
+  // correlation) when the table exists, else FP64
+  bool dft = false;
+  if constexpr (DF) dft = tab.twdf != nullptr;
+  if (dft) block_gs_apply_df<kFNT>(rho, Yf, x, N, log2M2, lr.delta_last, bufs, TwiddlesDF{tab.twdf, tab.log2max});
+  else block_gs_apply<kFNT>(rho, Yf, x, N, log2M2, lr.delta_last, bufs, tw);
   // Diagonal sums of C^{-1} (Sec. III-C, Appendix B):
   //   omega_s(i) = (1/d) sum_q [(q-c) + (q+i-c)] rho_q conj(rho_{q+i}),  |i| < N,
   // two cross-correlations; with P = FFT(rho) (still in bufs[0] after the
@@ -164,21 +169,51 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
   //   omega_s(i) = IFFT(2 Re(Pw conj(P)))(-i) / (d M2).
   {
     const double cen = 0.5 * (double)(N - 2);
-    const c128* P = bufs[0];
-    c128* Pw = bufs[1];
-    c128* G = bufs[2];
-    block_fft<kFNT, double>([=] __device__(int i) { return i < N ? ((double)i - cen) * rho[i] : zero<double>(); }, Pw,
-                            bufs[4], log2M2, false, tw);
-    block_fft<kFNT, double>([=] __device__(int k) { return mk(2.0 * (Pw[k] * conj(P[k])).re, 0.0); }, G, bufs[4],
-                            log2M2, true, tw);
     const double sc = 1.0 / (lr.delta_last * (double)(1 << log2M2));
     const int msk = (1 << log2M2) - 1;
     c128* om = omega_out + 2 * d.y_off;
     c64* om32 = omega32_out + 2 * d.y_off;
-    for (int i = (int)threadIdx.x - (N - 1); i <= N - 1; i += kFNT) {
-      const c128 v = sc * G[(-i) & msk];
-      om[i + N - 1] = v;
-      om32[i + N - 1] = cvt<float>(v);
+    if (dft) {
+      // P = FFT(rho) left in bufs[0] (double-float) by the apply
+      const float4* P = reinterpret_cast<const float4*>(bufs[0]);
+      float4* Pw = reinterpret_cast<float4*>(bufs[1]);
+      float4* G = reinterpret_cast<float4*>(bufs[2]);
+      float4* T = reinterpret_cast<float4*>(bufs[4]);
+      const TwiddlesDF twd{tab.twdf, tab.log2max};
+      const f2 cen2 = f2{(float)cen, 0.f};  // a half-integer below 2^24: exact
+      block_fft_df<kFNT>(
+          [=] __device__(int i) {
+            if (i >= N) return cf2_zero();
+            const cf2 r = cf2_of(rho[i]);
+            const f2 wi = sub_s(f2{(float)i, 0.f}, cen2);
+            return cf2{mul_f(wi, r.re), mul_f(wi, r.im)};
+          },
+          Pw, T, log2M2, false, twd);
+      block_fft_df<kFNT>(
+          [=] __device__(int k) {
+            const cf2 v = ld_cf2(Pw[k]) * conj(ld_cf2(P[k]));
+            return cf2{f2{2.f * v.re.h, 2.f * v.re.l}, f2{0.f, 0.f}};
+          },
+          G, T, log2M2, true, twd);
+      for (int i = (int)threadIdx.x - (N - 1); i <= N - 1; i += kFNT) {
+        const cf2 g = ld_cf2(G[(-i) & msk]);
+        const c128 v = mk(sc * to_d(g.re), sc * to_d(g.im));
+        om[i + N - 1] = v;
+        om32[i + N - 1] = cvt<float>(v);
+      }
+    } else {
+      const c128* P = bufs[0];
+      c128* Pw = bufs[1];
+      c128* G = bufs[2];
+      block_fft<kFNT, double>([=] __device__(int i) { return i < N ? ((double)i - cen) * rho[i] : zero<double>(); },
+                              Pw, bufs[4], log2M2, false, tw);
+      block_fft<kFNT, double>([=] __device__(int k) { return mk(2.0 * (Pw[k] * conj(P[k])).re, 0.0); }, G, bufs[4],
+                              log2M2, true, tw);
+      for (int i = (int)threadIdx.x - (N - 1); i <= N - 1; i += kFNT) {
+        const c128 v = sc * G[(-i) & msk];
+        om[i + N - 1] = v;
+        om32[i + N - 1] = cvt<float>(v);
+      }
     }
     c64* x32 = x32_out + d.y_off;
     for (int n = threadIdx.x; n < N; n += kFNT) x32[n] = cvt<float>(x[n]);
