@@ -666,6 +666,64 @@ __device__ void block_gs_apply_df(const c128* rho, const c128* Yf, c128* x, int 
 }
 
 // ---------------------------------------------------------------------------
+// block_first_column (Sec. III intro; C of eq. py) with the per-element sums
+// in double-float: c_m = beta [m = 0] + sum_k gamma_k e^{j2pi m theta_k}, the
+// shared tables gamma_k e^{j2pi l theta_k} and e^{j2pi S h theta_k} (m = S h
+// + l) formed in FP64 with exactly reduced phases and kept as double-float;
+// each (m, k) term is one double-float complex product, added with the
+// accurate double-float sum.  Output in FP64.  smem: KC*(S + H) complex
+// doubles, as for block_first_column.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ f2 add_a(f2 a, f2 b) {  // accurate double-float sum
+  f2 s = two_sum(a.h, b.h);
+  const f2 t = two_sum(a.l, b.l);
+  s = fast_two_sum(s.h, __fadd_rn(s.l, t.h));
+  return fast_two_sum(s.h, __fadd_rn(s.l, t.l));
+}
+
+template <int NT>
+__device__ void block_first_column_df(c128* c, const double* theta, const double* gamma, int K, double beta, int N,
+                                      c128* smem) {
+  int S, H;
+  first_column_split(N, S, H);
+  const int KC = kFirstColumnChunk;
+  float4* lo = reinterpret_cast<float4*>(smem);  // [KC][S]
+  float4* hi = lo + KC * S;                      // [KC][H]
+  float4* c4 = reinterpret_cast<float4*>(c);     // running sums, double-float in place
+  for (int m = threadIdx.x; m < N; m += NT) c4[m] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int k0 = 0; k0 < K; k0 += KC) {
+    const int kc = min(KC, K - k0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kc * S; i += NT) {
+      const int k = i / S, l = i - k * S;
+      const c128 v = gamma[k0 + k] * unit_phase((double)l, theta[k0 + k], 1.0);
+      lo[k * S + l] = pack(to_f2(v.re), to_f2(v.im));
+    }
+    for (int i = threadIdx.x; i < kc * H; i += NT) {
+      const int k = i / H, h = i - k * H;
+      const c128 v = unit_phase((double)h * S, theta[k0 + k], 1.0);
+      hi[k * H + h] = pack(to_f2(v.re), to_f2(v.im));
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m < N; m += NT) {
+      const int h = m / S, l = m - h * S;
+      cf2 acc = ld_cf2(c4[m]);
+      for (int k = 0; k < kc; ++k) {
+        const cf2 t = ld_cf2(lo[k * S + l]) * ld_cf2(hi[k * H + h]);
+        acc = cf2{add_a(acc.re, t.re), add_a(acc.im, t.im)};
+      }
+      c4[m] = st_cf2(acc);
+    }
+  }
+  __syncthreads();
+  for (int m = threadIdx.x; m < N; m += NT) {
+    const cf2 v = ld_cf2(c4[m]);
+    c[m] = mk((m == 0 ? beta : 0.0) + to_d(v.re), to_d(v.im));
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
 // Off-grid sums of block_active_sums (R_0..R_3 from rho, X_0..X_2 from x with
 // the centred weights (n - c)^a, phases e^{-j2pi n theta_k}) in double-float
 // on the FP32 pipes.  rho_df, x_df: the FP64 vectors converted once per

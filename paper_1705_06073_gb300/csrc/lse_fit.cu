@@ -211,7 +211,8 @@ struct Fitter {
   // (Levinson breakdown).
   __device__ int evaluate(const double* th, const double* ga, int K, bool want_sums) {
     const double beta = sh->beta;
-    block_first_column<kNT>(lev_c, th, ga, K, beta, N, tables);
+    if constexpr (PREC == 2) block_first_column_df<kNT>(lev_c, th, ga, K, beta, N, tables);
+    else block_first_column<kNT>(lev_c, th, ga, K, beta, N, tables);
     LevResult lr;
     if constexpr (PREC == 2) {
       if (A->cluster == 2 && lev_smem) lr = cluster_levinson();

@@ -112,7 +112,8 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
   } else {
     cc = (c128*)(base + FL.c); aa = (c128*)(base + FL.a); tables = (c128*)dsm;
   }
-  block_first_column<kFNT>(cc, theta + d.k_off, gamma + d.k_off, d.K, beta[b], N, tables);
+  if constexpr (DF) block_first_column_df<kFNT>(cc, theta + d.k_off, gamma + d.k_off, d.K, beta[b], N, tables);
+  else block_first_column<kFNT>(cc, theta + d.k_off, gamma + d.k_off, d.K, beta[b], N, tables);
   LevResult lr;
   if constexpr (DF) {
     if (csize > 1) {
