@@ -59,9 +59,12 @@ typedef enum lse_status {
  *   decision (argmin, approximate-activation candidates) is re-scored in
  *   FP64 before it is taken.  (FP32 Newton sums were measured to break the
  *   line search, so they stay FP64.)
- * LSE_PREC_MIXED_DF: as LSE_PREC_MIXED, but the Levinson recursion runs in
- *   double-float arithmetic (pairs of FP32 numbers, 48-bit significand) on
- *   the FP32 pipes, which on GB300 are ~70x faster than its FP64 pipe. */
+ * LSE_PREC_MIXED_DF: as LSE_PREC_MIXED, but the first column, the Levinson
+ *   recursion, the Gohberg-Semencul transforms and the off-grid Newton sums
+ *   run in double-float arithmetic (pairs of FP32 numbers, 48-bit
+ *   significand) on the FP32 pipes, which on GB300 are ~64x faster than its
+ *   FP64 pipe; the objective, beta and gamma updates stay FP64.  Grid
+ *   decisions are re-scored with the double-float off-grid sums. */
 enum { LSE_PREC_FP64 = 0, LSE_PREC_MIXED = 1, LSE_PREC_MIXED_DF = 2 };
 
 /* element type of grid outputs */
@@ -69,7 +72,7 @@ enum { LSE_F32 = 0, LSE_F64 = 1 };
 
 typedef struct lse_config {
   int32_t device;                  /* CUDA device ordinal */
-  int32_t precision;               /* LSE_PREC_FP64 or LSE_PREC_MIXED */
+  int32_t precision;               /* LSE_PREC_FP64, LSE_PREC_MIXED or LSE_PREC_MIXED_DF */
   uint64_t hbm_budget_bytes;       /* cap on the context's device workspace; 0 = no cap */
   int32_t grid_size;               /* L for lse_fit*: 0 = 8N rounded to the nearest power of two
                                       (Sec. II-C5 footnote); > 0: that L (a power of two >= 2N) */
@@ -261,7 +264,8 @@ LSE_API void lse_serve_destroy(lse_server* s);
  * not in the set, Sec. III-D).  Host pointers; y complex64 [2N]; theta, gamma
  * [K] (K >= 0); beta > 0; L a power of two with L >= 2N.  Outputs: q, dq, d2q
  * complex [2L], s, ds, d2s real [L], element type dtype (LSE_F64 for an
- * LSE_PREC_FP64 context, LSE_F32 for LSE_PREC_MIXED); any output may be NULL.
+ * LSE_PREC_FP64 context, LSE_F32 for LSE_PREC_MIXED and LSE_PREC_MIXED_DF);
+ * any output may be NULL.
  * Blocks until done. */
 LSE_API lse_status lse_eval_grid(lse_ctx* ctx, const float* y, int32_t N, const double* theta,
                          const double* gamma, int32_t K, double beta, int32_t L, int32_t dtype,
