@@ -142,6 +142,54 @@ def _exact_activation(st: _State, first=None):
     return n
 
 
+def approximate_activation_select(dl, q, s, gbar, zeta: float, theta_active, N: int, L: int, K_room: int):
+    """The candidate rules of the approximate multi-activation scheme (Sec. II-E,
+    reading R6), on one grid evaluation.
+
+    dl, q, s: Delta L (eq. delta_L), q and s at the grid points l/L; gbar: the
+    gamma-bar of that evaluation (a scalar, or one value per grid point when no
+    component is active, R4); theta_active: the frequencies active before the
+    pass; K_room: how many more components the model may hold (K_max - K).
+    Candidates are the cyclic local minima Delta L(l) < Delta L(l-1),
+    Delta L(l) <= Delta L(l+1) (a plateau keeps its first point).  With
+    Delta L_min the smallest candidate value, nothing happens unless
+    Delta L_min < 0; otherwise the candidates are visited in ascending
+    Delta L (ties by index) while Delta L <= Delta L_min / 5, and a candidate
+    is taken when its eq. (activate_gamma) value is > 0, eq. (activate_derived)
+    holds (no tau) and it lies at wrap distance >= 0.05/N from every active
+    frequency, those taken earlier in the same pass included.
+    Returns [(l, gamma_hat)] in the order taken."""
+    dl = np.asarray(dl, dtype=np.float64)
+    left = np.roll(dl, 1)
+    right = np.roll(dl, -1)
+    cand = np.nonzero((dl < left) & (dl <= right))[0]
+    if cand.size == 0:
+        return []
+    dlmin = float(np.min(dl[cand]))
+    if not dlmin < 0.0:
+        return []
+    order = cand[np.lexsort((cand, dl[cand]))]
+    taken = []
+    active = list(np.atleast_1d(np.asarray(theta_active, dtype=np.float64)))
+    for l in order:
+        if not dl[l] <= dlmin / 5.0:
+            break
+        if len(taken) >= K_room:
+            break
+        ghat = float(dn.activate_gamma(q[l], s[l]))
+        if not ghat > 0.0:
+            continue
+        gb = float(gbar if np.ndim(gbar) == 0 else gbar[l])
+        if not dn.activation_test(q[l], s[l], gb, zeta, 0.0):
+            continue
+        th = l / L
+        if active and np.min(_wrap(th, np.array(active))) < 0.05 / N:
+            continue
+        taken.append((int(l), ghat))
+        active.append(th)
+    return taken
+
+
 def _approximate_activation(st: _State):
     """R6: one pass of the approximate multi-activation scheme (Sec. II-E).
     Returns (number activated, grid data for reuse when nothing changed)."""
@@ -149,35 +197,12 @@ def _approximate_activation(st: _State):
         return 0, None
     grid = st.grid_delta()
     q, s, gbar, dl = grid
-    left = np.roll(dl, 1)
-    right = np.roll(dl, -1)
-    cand = np.nonzero((dl < left) & (dl <= right))[0]
-    if cand.size == 0:
-        return 0, grid
-    dlmin = float(np.min(dl[cand]))
-    if not dlmin < 0.0:
-        return 0, grid
-    order = cand[np.lexsort((cand, dl[cand]))]
-    n = 0
-    for l in order:
-        if not dl[l] <= dlmin / 5.0:
-            break
-        if st.K >= st.N:
-            break
-        ghat = float(dn.activate_gamma(q[l], s[l]))
-        if not ghat > 0.0:
-            continue
-        gb = float(gbar if np.ndim(gbar) == 0 else gbar[l])
-        if not dn.activation_test(q[l], s[l], gb, st.zeta, 0.0):
-            continue
-        th = l / st.L
-        if st.K and np.min(_wrap(th, st.theta)) < 0.05 / st.N:
-            continue
-        st.add(th, ghat)
-        n += 1
-    if n:
+    taken = approximate_activation_select(dl, q, s, gbar, st.zeta, st.theta, st.N, st.L, st.N - st.K)
+    for l, ghat in taken:
+        st.add(l / st.L, ghat)
+    if taken:
         st.refresh()
-    return n, grid
+    return len(taken), grid
 
 
 def _wrap(a, b):
@@ -215,17 +240,29 @@ def _newton_iteration(st: _State):
     return dec, False
 
 
+def deactivation_pick(stat, threshold: float):
+    """Which component one step of the deactivation of Sec. II-C4 removes
+    (reading R3): among those whose eq. (deactivate) statistic is below the
+    threshold ln((1 - zeta)/zeta), the one with the smallest statistic, whose
+    removal lowers eq. (obj) most (the change is statistic - threshold); ties go
+    to the lowest index, i.e. the earliest activated.  None if none qualifies."""
+    stat = np.asarray(stat, dtype=np.float64)
+    hit = np.nonzero(stat < threshold)[0]
+    if hit.size == 0:
+        return None
+    return int(hit[np.argmin(stat[hit])])
+
+
 def _deactivation(st: _State):
-    """R3: remove components meeting eq. (deactivate) one at a time."""
+    """R3: remove components meeting eq. (deactivate) one at a time, re-evaluating
+    the model after each removal ("repeated until no more can be deactivated")."""
     n = 0
     while st.K > 0:
         vec = st.ev.active_vectors()
         stat = dn.deactivation_statistic(vec["q"], vec["s"], st.gamma)
-        thr = dn.log_prior_odds(st.zeta)
-        hit = np.nonzero(stat < thr)[0]
-        if hit.size == 0:
+        k = deactivation_pick(stat, dn.log_prior_odds(st.zeta))
+        if k is None:
             break
-        k = int(hit[np.argmin(stat[hit])])
         st.theta = np.delete(st.theta, k)
         st.gamma = np.delete(st.gamma, k)
         st.refresh()
