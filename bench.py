@@ -6,11 +6,15 @@ superfast evaluations of Sec. III) of a batch of 64 synthetic instances with
 N = 4096 complex64 samples, K = 64 sinusoids (separation 2/N, alpha ~
 CN(0,1)), SNR uniform on [10, 30] dB per instance and an L = 4N = 16384
 point grid, in one launch of the persistent fit kernel.  The headline path
-is the mixed-precision one (FP64 Levinson recursion, generators, objective
-and updates; FP32 grid spectra and Newton sums); the plain FP64 path is
+is LSE_PREC_MIXED_DF: the first column, the generator recursion, the
+Gohberg-Semencul transforms and the off-grid Newton sums in double-float
+arithmetic on the FP32 pipes, the objective and the beta/gamma updates in
+FP64, the grid spectra in FP32 with every grid decision re-scored at the
+higher precision.  The plain FP64 path and the FP64-recursion mixed path are
 timed on the same batch beside it.  Grid-point throughput (first column,
-Levinson recursion, Gohberg-Semencul apply and all six grid outputs, Sec.
-IV-D) is measured on the same batch at the fitted states.
+recursion, Gohberg-Semencul apply and all six grid outputs, Sec. III-D) is
+measured on the same batch at the fitted states, and on the single
+N = 65536, L = 131072 instance at its true state.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank fits its own batch (weak scaling, no data-path
@@ -88,12 +92,38 @@ def fit_traffic(b: int):
     return FIT_TRAFFIC["bytes_per_instance"] * b
 
 
+# Measured copy bandwidth of the GB300s (GB/s); MEASURED_PEAKS.json
+# beside this file takes precedence when present.
+HBM_GBS_MEASURED = 6703.8
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json (STREAM-style copy, measured)"
+    except (OSError, KeyError, ValueError):
+        return HBM_GBS_MEASURED, "measured copy bandwidth of this pool's GB300s, recorded in bench.py"
+
+
+# DRAM traffic of grid_fft_kernel<float> per instance of the N = 4096,
+# L = 16384 batch (ncu dram__bytes_read.sum + dram__bytes_write.sum), with the
+# digest of the sources it was taken on; reported only while they match.
+GRID_TRAFFIC = {"sources_sha256": None, "bytes_per_instance": None}
+
+
+def grid_traffic(b: int):
+    if GRID_TRAFFIC["bytes_per_instance"] is None or GRID_TRAFFIC["sources_sha256"] != sources_digest():
+        return None
+    return GRID_TRAFFIC["bytes_per_instance"] * b
+
+
 def grid_bytes(n: int, l: int, f64: bool) -> float:
-    """Algorithmic bytes of one grid evaluation (Sec. III-D): read rho and x
-    (n complex128 each) and write q, q', q'' (complex) and s, s', s'' (real)
-    at l points."""
+    """Algorithmic bytes of one grid evaluation (Sec. III-D): read two length-n
+    complex sequences (the generator and x = C^-1 y; the index weights n^a are
+    generated, not read) and write q, q', q'' (complex) and s, s', s'' (real)
+    at l points: 16 n + 36 l bytes in FP32, twice that in FP64."""
     es = 8 if f64 else 4
-    return 2 * 16.0 * n + l * (3 * 2 * es + 3 * es)
+    return 2 * 2 * es * n + l * (3 * 2 * es + 3 * es)
 
 
 # ----------------------------------------------------------------- clocks ---
@@ -166,24 +196,36 @@ npts = int({L} * frac)
 t0 = time.perf_counter()
 ev.grid({L}, points=np.arange(npts) / {L})
 t_grid = (time.perf_counter() - t0) / frac
-# evaluations per fit of this instance family, counted by the oracle itself on
-# the same generator scaled down to N = {Np}, K = {Kp} (same K/N)
+counts = {counts!r}
 t0 = time.perf_counter()
-counts = []
-for s in range(2):
-    small = synth.make_instance({Np}, {Kp}, 10.0 + 20.0 * s, 201 + s)
-    r = ofit.fit(small.y, 4 * {Np})
-    counts.append((r.n_evals, r.n_grid_evals))
+if counts is None:
+    # evaluations per fit of this instance family, counted by the oracle itself
+    # on the same generator scaled down to N = {Np}, K = {Kp} (same K/N)
+    counts = []
+    for s in range(2):
+        small = synth.make_instance({Np}, {Kp}, 10.0 + 20.0 * s, 201 + s)
+        r = ofit.fit(small.y, 4 * {Np})
+        counts.append((r.n_evals, r.n_grid_evals))
+    ne = float(np.mean([c[0] for c in counts])); ng = float(np.mean([c[1] for c in counts]))
+    src = "oracle fits at N={Np}, K={Kp}"
+else:
+    ne, ng = counts
+    src = "the GPU fits of this workload"
 t_counts = time.perf_counter() - t0
-ne = float(np.mean([c[0] for c in counts])); ng = float(np.mean([c[1] for c in counts]))
-print(json.dumps(dict(t_eval=t_eval, t_grid=t_grid, n_evals=ne, n_grid=ng, t_counts=t_counts)))
+print(json.dumps(dict(t_eval=t_eval, t_grid=t_grid, n_evals=ne, n_grid=ng, t_counts=t_counts, count_source=src)))
 """
 
 
-def oracle_sample(threads: int, frac: float = 1 / 16):
+def oracle_sample(threads: int, frac: float = 1 / 16, counts=None):
+    """Time the dense oracle on one evaluation and a fraction of one grid
+    evaluation of a workload instance; per-fit cost = evaluations x t_eval +
+    grid evaluations x t_grid, with the counts given (those of the GPU run on
+    the same workload) or, without them, the oracle's own fits of a smaller
+    instance of the same family."""
     env = dict(os.environ, OPENBLAS_NUM_THREADS=str(threads), OMP_NUM_THREADS=str(threads),
                CUDA_VISIBLE_DEVICES="")
-    code = ORACLE_SAMPLE.format(root=ROOT, N=N, K=K, L=L, frac=frac, Np=512, Kp=8)
+    code = ORACLE_SAMPLE.format(root=ROOT, N=N, K=K, L=L, frac=frac, Np=512, Kp=8,
+                                counts=None if counts is None else (float(counts[0]), float(counts[1])))
     t0 = time.perf_counter()
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1800)
     wall = time.perf_counter() - t0
@@ -203,8 +245,7 @@ def cpu_desc(r, threads):
                        f"evaluation (Cholesky, ln|C|, C^-1 y, eqs. q-x) took {r['t_eval']:.3f} s and one "
                        f"{L}-point grid evaluation {r['t_grid']:.3f} s (timed on 1/{round(1 / r.get('frac', 1 / 16))} of the points, "
                        f"scaled); per-fit cost = {r['n_evals']:.1f} evaluations + {r['n_grid']:.1f} grid "
-                       f"evaluations, the counts of the oracle's own complete fits of the same generator "
-                       f"at N=512, K=8 (same K/N)")}
+                       f"evaluations, the mean counts of {r.get('count_source', 'oracle fits at N=512, K=8')}")}
 
 
 def run_reference(args, rank):
@@ -305,6 +346,57 @@ def ragged_leg(lse, dev):
             "n_range": [int(min(len(y) for y in ys)), int(max(len(y) for y in ys))]}
 
 
+def c3_grid_leg(lse, dev, steps, warmup, flush):
+    """Eval-grid of the single N = 65536, K = 512, L = 131072 instance (15 dB,
+    |alpha| log-uniform over 30 dB, separation 1.5/N) at its true state, on
+    the headline path: factorisation + all six FP32 grid outputs per step."""
+    import numpy as _np
+    import torch as _torch
+    from paper_1705_06073_gb300 import synth
+    inst, Lc = synth.single_n65536()[0]
+    Nc = len(inst.y)
+    y_d = _torch.from_numpy(inst.y).to(dev)
+    th_d = _torch.from_numpy(_np.ascontiguousarray(inst.theta)).to(dev)
+    ga_d = _torch.from_numpy(_np.abs(inst.alpha) ** 2).to(dev)
+    be_d = _torch.tensor([inst.beta], dtype=_torch.float64, device=dev)
+    yo = _np.array([0, Nc], _np.int64)
+    ko = _np.array([0, len(inst.theta)], _np.int64)
+    Ls = _np.array([Lc], _np.int32)
+    outs = {f: _torch.empty(Lc, dtype=_torch.complex64 if f in ("q", "dq", "d2q") else _torch.float32, device=dev)
+            for f in ("q", "dq", "d2q", "s", "ds", "d2s")}
+    ctx = lse.lse_create(lse.lse_config_default(device=dev.index or 0, precision=lse.LSE_PREC_MIXED_DF))
+    st = _torch.cuda.Stream(device=dev)
+    try:
+        for _ in range(warmup):
+            lse.lse_eval_grid_batch_d(ctx, y_d, yo, th_d, ga_d, ko, be_d, Ls, outs, False, st)
+        st.synchronize()
+        lse.lse_kernel_time(ctx, 1)
+        lse.lse_kernel_time(ctx, 2)
+        ms = []
+        for _ in range(steps):
+            with _torch.cuda.stream(st):
+                flush.zero_()
+                e0 = _torch.cuda.Event(enable_timing=True)
+                e1 = _torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                lse.lse_eval_grid_batch_d(ctx, y_d, yo, th_d, ga_d, ko, be_d, Ls, outs, False, st)
+                e1.record(st)
+            st.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        fms, fl = lse.lse_kernel_time(ctx, 1)
+        gms, gl = lse.lse_kernel_time(ctx, 2)
+    finally:
+        lse.lse_destroy(ctx)
+    peak, _src = hbm_peak()
+    g_ms = gms / max(gl, 1)
+    ach = grid_bytes(Nc, Lc, False) / (g_ms / 1e3) / 1e9
+    return {"workload": "single_n65536_k512_l131072", "value": Lc * steps / (sum(ms) / 1e3),
+            "unit": "grid-pt evals/s", "ms_per_eval": sum(ms) / steps, "factor_kernel_ms": fms / max(fl, 1),
+            "grid_kernel_ms": g_ms,
+            "roofline_grid": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                              "bytes_per_launch": grid_bytes(Nc, Lc, False)}}
+
+
 # -------------------------------------------------------------- GPU arm ---
 def main():
     ap = argparse.ArgumentParser()
@@ -321,6 +413,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=0.02,
                     help="arrival window of the serving leg (Poisson, 2000 req/s); 0 skips it")
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged 1024-instance graph launch")
+    ap.add_argument("--no-c3", action="store_true", help="skip the N = 65536 eval-grid leg")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -416,7 +509,7 @@ def main():
         Kf = out["K"].cpu().numpy()
         total_ms = max_over_ranks(sum(ms))
         res[name] = dict(ms=ms, total_ms=total_ms, kernel_ms=kms / max(launches, 1), launches=launches,
-                         n_evals=n_ev, n_grid=n_gr, status=st, K=Kf,
+                         n_evals=n_ev, n_grid=n_gr, status=st, K=Kf, iters=out["iters"].cpu().numpy(),
                          value=sum_over_ranks(Bn * args.steps) / (total_ms / 1e3), out=out)
 
     # ---- grid-point throughput at the fitted states (factor + grid kernels)
@@ -486,6 +579,7 @@ def main():
 
     serving = serve_leg(lse, args.serve_seconds, local) if args.serve_seconds > 0 and rank == 0 else None
     ragged = ragged_leg(lse, dev) if not args.no_ragged and rank == 0 else None
+    c3 = c3_grid_leg(lse, dev, args.steps, args.warmup, flush) if not args.no_c3 and rank == 0 else None
 
     if rank != 0:
         if dist:
@@ -493,17 +587,23 @@ def main():
         return
 
     m = res[HEAD]
-    # Levinson flops of one launch: every instance's evaluations in that fit
-    fit_flops = float(np.sum(m["n_evals"])) * levinson_df_flops(N)
-    achieved = fit_flops / (m["kernel_ms"] / 1e3) / 1e12
+    # algorithmic flops of one launch (8 N^2 per factorisation of C, the
+    # recursion's count): every instance's evaluations in that fit
+    kernel_s = m["kernel_ms"] / 1e3
+    fit_flops = float(np.sum(m["n_evals"])) * levinson_flops(N)
+    achieved = fit_flops / kernel_s / 1e12
+    df_instr = float(np.sum(m["n_evals"])) * levinson_df_flops(N) / kernel_s / 1e12
     cpu = None
     if not args.no_cpu:
         threads = os.cpu_count() or 1
         try:
-            cpu = cpu_desc(oracle_sample(threads), threads)
+            counts = (float(np.mean(m["n_evals"])), float(np.mean(m["n_grid"])))
+            cpu = cpu_desc(oracle_sample(threads, counts=counts), threads)
         except Exception as e:  # the baseline is reported, never required
             cpu = {"value": None, "error": str(e)[:300]}
     gm = grid[HEAD]
+    peak_gbs, peak_src = hbm_peak()
+    g_ach = Bn * grid_bytes(N, L, False) / (gm["grid_ms"] / 1e3) / 1e9
     line = {
         "metric": METRIC,
         "value": m["value"],
@@ -524,10 +624,18 @@ def main():
         "e2e": {"value": e2e_val, "unit": "fitted instances/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": fit_traffic(Bn),
-                     "kernel": "fit_kernel<2> (double-float Levinson recursion dominates; clusters of two blocks when 2B <= 152)",
-                     "peak_source": "FP32 pipe: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived)",
+                     "kernel": "fit_kernel<2> (the generator recursion dominates; clusters of two blocks when 2B <= 152)",
+                     "algorithmic_flops": "8 N^2 per factorisation of C (the Levinson count) x factorisations in the launch",
+                     "peak_source": "FP32 pipe, which the double-float kernel runs on: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived)",
+                     "frac_of_fp64_pipe": achieved / FP64_PEAK_TFLOPS,
+                     "df_instruction_tflops": df_instr,
                      "sms_busy": 2 * Bn if 2 * Bn <= 152 else min(Bn, 152)},
-        "fit": {"iters_mean": None, "n_evals_mean": float(np.mean(m["n_evals"])),
+        "roofline_grid": {"bound": "hbm", "achieved": g_ach, "peak": peak_gbs, "unit": "GB/s",
+                          "frac": g_ach / peak_gbs, "traffic": grid_traffic(Bn),
+                          "kernel": "grid_fft_kernel<float> (a4+a5 of lse_eval_grid, all six outputs)",
+                          "algorithmic_bytes": "(16 N + 36 L) per instance", "peak_source": peak_src},
+        "c3_grid": c3,
+        "fit": {"iters_mean": float(np.mean(m["iters"])), "n_evals_mean": float(np.mean(m["n_evals"])),
                 "n_grid_mean": float(np.mean(m["n_grid"])), "K_mean": float(np.mean(m["K"])),
                 "status_nonzero": int(np.count_nonzero(m["status"])), "fit_kernel_ms": m["kernel_ms"]},
         "grid_pt_evals": {"value": gm["value"], "unit": "grid-pt evals/s", "ms_per_batch": gm["ms"],

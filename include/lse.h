@@ -173,7 +173,14 @@ LSE_API lse_status lse_fit_batch(lse_ctx* ctx, const float* y, const int64_t* of
 /* Device-pointer batched fit.  y_d: device complex64 batch; offsets: HOST
  * array [B+1] as in lse_fit_batch; out: device arrays (lse_batch_out).
  * stream: cudaStream_t (NULL = the context's stream).  Asynchronous: the
- * results are valid once the stream has reached this point. */
+ * results are valid once the stream has reached this point.  The call does
+ * not wait for the device, except when the context must grow its device
+ * memory or twiddle tables (a larger shape than any before).  Launch
+ * descriptors are uploaded only when they differ from the previous call's.
+ * The call may be stream-captured once a call with the same offsets has run
+ * outside capture (nothing is then allocated or uploaded); otherwise it
+ * returns LSE_EINVAL during capture.  While capturing, ordering against the
+ * context's own stream is left to the caller. */
 LSE_API lse_status lse_fit_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* offsets, int32_t B,
                            const lse_batch_out* out, void* stream);
 
@@ -278,7 +285,13 @@ LSE_API lse_status lse_eval_grid(lse_ctx* ctx, const float* y, int32_t N, const 
  * [B].  L: HOST int32 [B], each a power of two >= 2 N_b.  Outputs (device,
  * any may be NULL): instance b's grid occupies [g_b, g_b + L_b) with g_b the
  * prefix sum of L (complex outputs count complex elements).  dtype as for
- * lse_eval_grid.  Asynchronous on stream (NULL = the context's stream). */
+ * lse_eval_grid.  Asynchronous on stream (NULL = the context's stream): the
+ * call does not wait for the device except when the context must grow its
+ * device memory or twiddle tables, and on the first batch of a new (element
+ * type, L), which the grid-FFT autotuner times (LSE_FLAG_NO_AUTOTUNE).  The
+ * factorisation and grid kernels may be stream-captured once a call with the
+ * same shapes (offsets, L, the set of non-NULL outputs) has run outside
+ * capture; otherwise the call returns LSE_EINVAL during capture. */
 LSE_API lse_status lse_eval_grid_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* y_offsets,
                                  int32_t B, const double* theta_d, const double* gamma_d,
                                  const int64_t* k_offsets, const double* beta_d,
@@ -318,15 +331,22 @@ LSE_API lse_status lse_kernel_time(lse_ctx* ctx, int32_t which, double* total_ms
  * the library's 8 MiB static scratch array; anything larger returns
  * LSE_EINVAL before any work is enqueued.
  *
+ * Every precision runs the arithmetic of lse_fit_batch_d with the same
+ * configuration (the library's own twiddle tables are static arrays too).
+ * cfg->flags accepts the LSE_FLAG_* bits only; grid_size must be >= 0.
+ *
  * The scratch is a fixed array inside the library, present on every GPU
  * that loads it until the process exits, and shared by all calls: calls
  * whose work overlaps on the GPU (other streams, other host threads) race
  * on it, so serialise them.  Each call clears what must start at zero (the
- * launch's work counter); the rest keeps the previous call's contents and
- * is rewritten before it is read.  The first call on a device does a
- * one-time set-up there (looking up the device addresses of the static
- * arrays and filling a twiddle table); make that first call before any
- * stream capture. */
+ * launch's work counter, written together with the launch descriptor by a
+ * small kernel that takes them as parameters); the rest keeps the previous
+ * call's contents and is rewritten before it is read.  The first call on a
+ * device does a one-time set-up there: it looks up the device addresses of
+ * the static arrays, fills the twiddle tables on its stream and waits for
+ * that fill; make that first call before any stream capture.  The addresses
+ * belong to the device's primary context: do not use this entry point after
+ * cudaDeviceReset. */
 LSE_API lse_status lse_fit_noalloc_d(const lse_config* cfg, const float* y_d, int32_t N,
                                      const lse_batch_out* out, void* stream);
 

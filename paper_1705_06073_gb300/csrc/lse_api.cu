@@ -27,6 +27,19 @@ struct DevBuf {
   size_t n = 0;
 };
 
+// Launch metadata (instance descriptors, grid offsets, task lists) kept on the
+// device: uploaded only when its content changes, from one of two pinned
+// host slots whose previous upload is known complete (its event), so a call
+// never waits on the device for it.
+struct Staged {
+  DevBuf dev;
+  std::vector<char> last;  // what dev holds
+  char* pinned[2] = {nullptr, nullptr};
+  size_t pcap[2] = {0, 0};
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int next = 0;
+};
+
 }  // namespace
 
 struct lse_plan;
@@ -40,10 +53,9 @@ struct lse_ctx {
   c64* tw32 = nullptr;
   float4* twdf = nullptr;
   int log2max = 0;
-  DevBuf ws, desc, counter, stage_in, stage_out, fac, tasks;
+  DevBuf ws, counter, stage_in, stage_out, fac;
+  Staged fit_meta, grid_meta;
   size_t allocated = 0;
-  InstDesc* h_desc = nullptr;  // pinned
-  size_t h_desc_cap = 0;
   std::vector<TimedLaunch> timed[3];
   std::string err;
   // autotuned schedule of the on-chip grid FFT per (FP32?, L)
@@ -77,8 +89,11 @@ lse_status cuda_fail(lse_ctx* c, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
   } while (0)
 
-lse_status ensure(lse_ctx* c, DevBuf& b, size_t bytes) {
+lse_status ensure(lse_ctx* c, DevBuf& b, size_t bytes, bool capturing = false) {
   if (b.n >= bytes) return LSE_OK;
+  if (capturing)
+    return fail(c, LSE_EINVAL, "the call needs more device memory than the context holds, which cannot be "
+                               "allocated during stream capture: make one call with these shapes first");
   const size_t grow = bytes - b.n;
   if (c->cfg.hbm_budget_bytes && c->allocated + grow > c->cfg.hbm_budget_bytes)
     return fail(c, LSE_EBUDGET, "request needs " + std::to_string(c->allocated + grow) +
@@ -145,24 +160,61 @@ int default_L(int N) {
 
 bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
 
-lse_status stage_desc(lse_ctx* c, const std::vector<InstDesc>& d) {
-  const size_t bytes = d.size() * sizeof(InstDesc);
-  if (c->h_desc_cap < d.size()) {
-    if (c->h_desc) cudaFreeHost(c->h_desc);
-    c->h_desc = nullptr;
-    LSE_CUDA(c, cudaMallocHost(&c->h_desc, bytes));
-    c->h_desc_cap = d.size();
+bool is_capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
+// Make s.dev hold `bytes` of `data`, enqueuing the upload on st if it does not
+// already.  Stream order protects the device copy (every launch that reads it
+// is ordered before the next upload); the pinned slot is reused only after
+// the upload that last read it has completed.
+lse_status stage(lse_ctx* c, Staged& s, const void* data, size_t bytes, cudaStream_t st, bool capturing) {
+  if (s.dev.p && s.last.size() == bytes && std::memcmp(s.last.data(), data, bytes) == 0) return LSE_OK;
+  if (capturing)
+    return fail(c, LSE_EINVAL, "launch descriptors differ from the previous call's, and uploading them cannot be "
+                               "captured: make one call with these shapes before capturing");
+  lse_status r = ensure(c, s.dev, bytes);
+  if (r) return r;
+  const int k = s.next;
+  s.next ^= 1;
+  if (!s.ev[k]) LSE_CUDA(c, cudaEventCreateWithFlags(&s.ev[k], cudaEventDisableTiming));
+  else LSE_CUDA(c, cudaEventSynchronize(s.ev[k]));
+  if (s.pcap[k] < bytes) {
+    if (s.pinned[k]) cudaFreeHost(s.pinned[k]);
+    s.pinned[k] = nullptr;
+    s.pcap[k] = 0;
+    LSE_CUDA(c, cudaMallocHost((void**)&s.pinned[k], bytes));
+    s.pcap[k] = bytes;
   }
-  lse_status s = ensure(c, c->desc, bytes);
-  if (s) return s;
-  // the previous launch may still read the pinned staging copy
-  LSE_CUDA(c, cudaStreamSynchronize(c->stream));
-  std::memcpy(c->h_desc, d.data(), bytes);
-  LSE_CUDA(c, cudaMemcpyAsync(c->desc.p, c->h_desc, bytes, cudaMemcpyHostToDevice, c->stream));
+  std::memcpy(s.pinned[k], data, bytes);
+  LSE_CUDA(c, cudaMemcpyAsync(s.dev.p, s.pinned[k], bytes, cudaMemcpyHostToDevice, st));
+  LSE_CUDA(c, cudaEventRecord(s.ev[k], st));
+  s.last.assign((const char*)data, (const char*)data + bytes);
+  return LSE_OK;
+}
+
+void release(Staged& s) {
+  if (s.dev.p) cudaFree(s.dev.p);
+  for (int k = 0; k < 2; ++k) {
+    if (s.pinned[k]) cudaFreeHost(s.pinned[k]);
+    if (s.ev[k]) cudaEventDestroy(s.ev[k]);
+  }
+}
+
+// `from` waits for everything enqueued so far on `to`'s side: used to order a
+// caller stream after the context stream and back.
+lse_status order_after(lse_ctx* c, cudaStream_t waiter, cudaStream_t done) {
+  cudaEvent_t e;
+  LSE_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaEventRecord(e, done);
+  cudaStreamWaitEvent(waiter, e, 0);
+  cudaEventDestroy(e);
   return LSE_OK;
 }
 
 void record(lse_ctx* c, int which, cudaStream_t st, bool start) {
+  if (is_capturing(st)) return;  // events recorded into a graph carry no time
   if (start) {
     TimedLaunch t;
     cudaEventCreate(&t.a);
@@ -296,12 +348,13 @@ void lse_destroy(lse_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->cfg.device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  for (DevBuf* b : {&ctx->ws, &ctx->desc, &ctx->counter, &ctx->stage_in, &ctx->stage_out, &ctx->fac, &ctx->tasks})
+  for (DevBuf* b : {&ctx->ws, &ctx->counter, &ctx->stage_in, &ctx->stage_out, &ctx->fac})
     if (b->p) cudaFree(b->p);
+  release(ctx->fit_meta);
+  release(ctx->grid_meta);
   if (ctx->tw64) cudaFree(ctx->tw64);
   if (ctx->tw32) cudaFree(ctx->tw32);
   if (ctx->twdf) cudaFree(ctx->twdf);
-  if (ctx->h_desc) cudaFreeHost(ctx->h_desc);
   for (auto& v : ctx->timed)
     for (auto& t : v) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -333,41 +386,33 @@ lse_status lse_fit_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* offset
   if (offsets[0] != 0) return fail(ctx, LSE_EINVAL, "offsets[0] must be 0");
   cudaSetDevice(ctx->cfg.device);
   cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+  const bool cap = is_capturing(st);
   std::vector<InstDesc> d;
   int Nmax = 0, Lmax = 0;
   lse_status s = plan_fit_descs(ctx, offsets, B, d, Nmax, Lmax);
   if (s) return s;
   const int prec = ctx->cfg.precision;
-  if ((s = ensure_tables(ctx, std::max(ilog2((uint32_t)Lmax), ilog2(2u * (uint32_t)Nmax))))) return s;
+  const int log2t = std::max(ilog2((uint32_t)Lmax), ilog2(2u * (uint32_t)Nmax));
+  if (cap && (!ctx->tw64 || ctx->log2max < log2t))
+    return fail(ctx, LSE_EINVAL, "twiddle tables must grow, which cannot be captured: make one call first");
+  if ((s = ensure_tables(ctx, log2t))) return s;
   const int grid = std::min(B, ctx->sm_count);
   const size_t per = fit_workspace_bytes(Nmax, Lmax, prec);
-  if ((s = ensure(ctx, ctx->ws, per * grid))) return s;
-  if ((s = stage_desc(ctx, d))) return s;
-  if (st != ctx->stream) {
-    cudaEvent_t e;
-    LSE_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    cudaEventRecord(e, ctx->stream);
-    cudaStreamWaitEvent(st, e, 0);
-    cudaEventDestroy(e);
-  }
+  if ((s = ensure(ctx, ctx->ws, per * grid, cap))) return s;
+  if (!cap && st != ctx->stream && (s = order_after(ctx, st, ctx->stream))) return s;
+  if ((s = stage(ctx, ctx->fit_meta, d.data(), d.size() * sizeof(InstDesc), st, cap))) return s;
   LSE_CUDA(ctx, cudaMemsetAsync(ctx->counter.p, 0, sizeof(int), st));
   FitConfig fc{ctx->cfg.tau, ctx->cfg.max_outer, ctx->cfg.max_inner, ctx->cfg.approx_activation_iters,
                !(ctx->cfg.flags & LSE_FLAG_NO_CLUSTER)};
   FitOut fo{out->theta, out->gamma, (c128*)out->alpha, out->K, out->beta, out->objective, out->iters,
             out->n_evals, out->n_grid, out->status};
   record(ctx, 0, st, true);
-  cudaError_t e = launch_fit(prec, y_d, (const InstDesc*)ctx->desc.p, B, Nmax, Lmax, fc, tables(ctx), fo, ctx->ws.p,
-                             (int*)ctx->counter.p, grid, st);
+  cudaError_t e = launch_fit(prec, y_d, (const InstDesc*)ctx->fit_meta.dev.p, B, Nmax, Lmax, fc, tables(ctx), fo,
+                             ctx->ws.p, (int*)ctx->counter.p, grid, st);
   record(ctx, 0, st, false);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "fit kernel launch");
-  if (st != ctx->stream) {
-    // later host-side staging on the context stream must follow this launch
-    cudaEvent_t ev;
-    LSE_CUDA(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    cudaEventRecord(ev, st);
-    cudaStreamWaitEvent(ctx->stream, ev, 0);
-    cudaEventDestroy(ev);
-  }
+  // later work of this context on its own stream must follow this launch
+  if (!cap && st != ctx->stream && (s = order_after(ctx, ctx->stream, st))) return s;
   return LSE_OK;
 }
 
@@ -541,6 +586,7 @@ lse_status lse_eval_grid_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* 
     return fail(ctx, LSE_EINVAL, "dtype must be LSE_F64 for an FP64 context and LSE_F32 for a mixed one");
   cudaSetDevice(ctx->cfg.device);
   cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+  const bool cap = is_capturing(st);
   std::vector<InstDesc> d(B);
   int Nmax = 0, Lmax = 0;
   int64_t g = 0;
@@ -555,31 +601,39 @@ lse_status lse_eval_grid_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* 
     Nmax = std::max(Nmax, (int)n);
     Lmax = std::max(Lmax, (int)L[b]);
   }
-  lse_status sst = ensure_tables(ctx, std::max(ilog2((uint32_t)Lmax), ilog2(2u * (uint32_t)Nmax)));
+  const int log2t = std::max(ilog2((uint32_t)Lmax), ilog2(2u * (uint32_t)Nmax));
+  if (cap && (!ctx->tw64 || ctx->log2max < log2t))
+    return fail(ctx, LSE_EINVAL, "twiddle tables must grow, which cannot be captured: make one call first");
+  lse_status sst = ensure_tables(ctx, log2t);
   if (sst) return sst;
   const int64_t totN = y_offsets[B];
   const size_t fws = factor_workspace_bytes(Nmax) * B;
-  const size_t gws_hdr = ((size_t)B * sizeof(int64_t) + 255) & ~size_t(255);
   const size_t gws = grid_workspace_bytes(B, g, f32);
   const size_t fac_bytes =
       (size_t)totN * (4 * sizeof(c128) + 3 * sizeof(c64)) + (size_t)B * (sizeof(double) + sizeof(int)) + 1024;
-  if ((sst = ensure(ctx, ctx->ws, std::max(fws, gws_hdr + gws)))) return sst;
-  if ((sst = ensure(ctx, ctx->fac, fac_bytes))) return sst;
-  if ((sst = stage_desc(ctx, d))) return sst;
-  // grid workspace offsets (bytes from the workspace base)
-  std::vector<int64_t> woff(B);
+  if ((sst = ensure(ctx, ctx->ws, std::max(fws, gws), cap))) return sst;
+  if ((sst = ensure(ctx, ctx->fac, fac_bytes, cap))) return sst;
+  // launch metadata, one block: descriptors | grid workspace offsets (bytes
+  // from the workspace base, global-memory grid kernel) | on-chip task list
+  std::vector<int4> tasks(5 * (size_t)B);
+  const int ntasks = grid_tasks(d.data(), B, q, dq, d2q, s, ds, d2s, tasks.data());
+  const size_t desc_b = ((size_t)B * sizeof(InstDesc) + 15) & ~size_t(15);
+  const size_t woff_b = ((size_t)B * sizeof(int64_t) + 15) & ~size_t(15);
+  std::vector<char> meta(desc_b + woff_b + (size_t)ntasks * sizeof(int4), 0);
+  std::memcpy(meta.data(), d.data(), (size_t)B * sizeof(InstDesc));
   {
-    size_t o = gws_hdr;
+    int64_t* woff = reinterpret_cast<int64_t*>(meta.data() + desc_b);
+    size_t o = 0;
     const size_t es = f32 ? sizeof(c64) : sizeof(c128);
     for (int b = 0; b < B; ++b) { woff[b] = (int64_t)o; o += (size_t)L[b] * 2 * 5 * es; }
   }
-  if (st != ctx->stream) {
-    cudaEvent_t e;
-    LSE_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    cudaEventRecord(e, ctx->stream);
-    cudaStreamWaitEvent(st, e, 0);
-    cudaEventDestroy(e);
-  }
+  std::memcpy(meta.data() + desc_b + woff_b, tasks.data(), (size_t)ntasks * sizeof(int4));
+  if (!cap && st != ctx->stream && (sst = order_after(ctx, st, ctx->stream))) return sst;
+  if ((sst = stage(ctx, ctx->grid_meta, meta.data(), meta.size(), st, cap))) return sst;
+  const char* mdev = (const char*)ctx->grid_meta.dev.p;
+  const InstDesc* desc_d = (const InstDesc*)mdev;
+  const int64_t* woff_d = (const int64_t*)(mdev + desc_b);
+  const int4* tasks_d = (const int4*)(mdev + desc_b + woff_b);
   c128* rho = (c128*)ctx->fac.p;
   c128* x = rho + totN;
   c128* omega = x + totN;  // 2N per instance (2N-1 used)
@@ -588,34 +642,27 @@ lse_status lse_eval_grid_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* 
   c64* omega32 = (c64*)(((uintptr_t)(status + B) + 255) & ~(uintptr_t)255);
   c64* x32 = omega32 + 2 * totN;
   record(ctx, 1, st, true);
-  cudaError_t e = launch_factor(ctx->cfg.precision == LSE_PREC_MIXED_DF, y_d, (const InstDesc*)ctx->desc.p, B, Nmax, theta_d, gamma_d, beta_d, tables(ctx),
-                                ctx->ws.p, rho, x, omega, omega32, x32, delta, status,
+  cudaError_t e = launch_factor(ctx->cfg.precision == LSE_PREC_MIXED_DF, y_d, desc_d, B, Nmax, theta_d, gamma_d, beta_d,
+                                tables(ctx), ctx->ws.p, rho, x, omega, omega32, x32, delta, status,
                                 !(ctx->cfg.flags & LSE_FLAG_NO_CLUSTER), st);
   record(ctx, 1, st, false);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "factor kernel launch");
-  // the grid kernel reuses the workspace; its offset table goes first
-  LSE_CUDA(ctx, cudaMemcpyAsync(ctx->ws.p, woff.data(), B * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-  // task list of the on-chip grid kernel
-  std::vector<int4> tasks(5 * (size_t)B);
-  const int ntasks = grid_tasks(d.data(), B, q, dq, d2q, s, ds, d2s, tasks.data());
-  if ((sst = ensure(ctx, ctx->tasks, std::max<size_t>(1, ntasks) * sizeof(int4)))) return sst;
-  LSE_CUDA(ctx, cudaMemcpyAsync(ctx->tasks.p, tasks.data(), ntasks * sizeof(int4), cudaMemcpyHostToDevice, st));
-  LSE_CUDA(ctx, cudaStreamSynchronize(st));  // the host task vector goes out of scope
   // schedule of the on-chip grid FFT: cached, or tuned now on this batch
+  // (tuning waits for the device once; it is skipped while capturing)
   int variant = 1;
   if (grid_on_chip(f32, Lmax)) {
     const auto key = std::make_pair(f32 ? 1 : 0, Lmax);
     auto it = ctx->grid_variant.find(key);
     if (it != ctx->grid_variant.end()) {
       variant = it->second;
-    } else if (!(ctx->cfg.flags & LSE_FLAG_NO_AUTOTUNE)) {
+    } else if (!(ctx->cfg.flags & LSE_FLAG_NO_AUTOTUNE) && !cap) {
       const int nv = grid_variant_count();
       std::vector<cudaEvent_t> ev(nv + 1);
       for (auto& x : ev) LSE_CUDA(ctx, cudaEventCreate(&x));
       cudaEventRecord(ev[0], st);
       for (int v = 0; v < nv; ++v) {
-        e = launch_grid(v, f32, (const InstDesc*)ctx->desc.p, B, Lmax, rho, x, omega, x32, omega32, delta,
-                        tables(ctx), ctx->ws.p, (const int4*)ctx->tasks.p, ntasks, q, dq, d2q, s, ds, d2s, st);
+        e = launch_grid(v, f32, desc_d, B, Lmax, rho, x, omega, x32, omega32, delta, tables(ctx), ctx->ws.p, woff_d,
+                        tasks_d, ntasks, q, dq, d2q, s, ds, d2s, st);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "grid kernel launch (autotune)");
         cudaEventRecord(ev[v + 1], st);
       }
@@ -632,17 +679,11 @@ lse_status lse_eval_grid_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* 
     }
   }
   record(ctx, 2, st, true);
-  e = launch_grid(variant, f32, (const InstDesc*)ctx->desc.p, B, Lmax, rho, x, omega, x32, omega32, delta,
-                  tables(ctx), ctx->ws.p, (const int4*)ctx->tasks.p, ntasks, q, dq, d2q, s, ds, d2s, st);
+  e = launch_grid(variant, f32, desc_d, B, Lmax, rho, x, omega, x32, omega32, delta, tables(ctx), ctx->ws.p, woff_d,
+                  tasks_d, ntasks, q, dq, d2q, s, ds, d2s, st);
   record(ctx, 2, st, false);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "grid kernel launch");
-  if (st != ctx->stream) {
-    cudaEvent_t ev;
-    LSE_CUDA(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    cudaEventRecord(ev, st);
-    cudaStreamWaitEvent(ctx->stream, ev, 0);
-    cudaEventDestroy(ev);
-  }
+  if (!cap && st != ctx->stream && (sst = order_after(ctx, ctx->stream, st))) return sst;
   return LSE_OK;
 }
 

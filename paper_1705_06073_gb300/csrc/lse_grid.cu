@@ -497,15 +497,14 @@ bool grid_on_chip(bool f32, int Lmax) { return Lmax <= (f32 ? grid_mmax<float>()
 
 cudaError_t launch_grid(int variant, bool f32, const InstDesc* inst, int B, int Lmax, const c128* rho, const c128* x,
                         const c128* omega, const c64* x32, const c64* omega32, const double* delta, const Tables& tab,
-                        void* ws, const int4* tasks, int ntasks, void* q, void* dq, void* d2q, void* s, void* ds,
-                        void* d2s, cudaStream_t stream) {
+                        void* ws, const int64_t* ws_off, const int4* tasks, int ntasks, void* q, void* dq, void* d2q,
+                        void* s, void* ds, void* d2s, cudaStream_t stream) {
   if (grid_on_chip(f32, Lmax))
     return f32 ? launch_grid_fft<float>(variant, inst, tasks, ntasks, omega32, x32, tab, Lmax, q, dq, d2q, s, ds, d2s,
                                         stream)
                : launch_grid_fft<double>(variant, inst, tasks, ntasks, omega, x, tab, Lmax, q, dq, d2q, s, ds, d2s,
                                          stream);
-  // ws begins with B int64 offsets (per instance, bytes) followed by buffers
-  const int64_t* ws_off = (const int64_t*)ws;
+  // instance b's buffers start ws_off[b] bytes into ws
   char* base = (char*)ws;
   if (f32)
     grid_kernel<float><<<2 * B, kFNT, 0, stream>>>(inst, rho, x, delta, tab, base, ws_off, (float*)q, (float*)dq,

@@ -81,10 +81,12 @@ GridVariant grid_variant(int i);
 
 // rho, x: [sum N]; omega: instance b's 2N-1 diagonal sums at 2*y_off.
 // variant: index of the on-chip schedule (ignored for grids too large for it).
+// ws, ws_off (device, B entries): workspace of the global-memory grid kernel,
+// instance b's buffers ws_off[b] bytes into ws (unused by the on-chip kernel).
 cudaError_t launch_grid(int variant, bool f32, const InstDesc* inst, int B, int Lmax, const c128* rho, const c128* x,
                         const c128* omega, const c64* x32, const c64* omega32, const double* delta, const Tables& tab,
-                        void* ws, const int4* tasks, int ntasks, void* q, void* dq, void* d2q, void* s, void* ds,
-                        void* d2s, cudaStream_t stream);
+                        void* ws, const int64_t* ws_off, const int4* tasks, int ntasks, void* q, void* dq, void* d2q,
+                        void* s, void* ds, void* d2s, cudaStream_t stream);
 // The on-chip grid kernel's task list for a batch (host): one block per
 // (instance, output family); the s'' transforms of consecutive instances of
 // equal N and L share one block.  `out` needs 5 B entries; returns the count.

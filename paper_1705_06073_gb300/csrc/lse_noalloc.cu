@@ -34,9 +34,11 @@ constexpr int kMaxDevices = 64;
 
 // Workspace of the one block that runs the fit.  Shared by every call.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
-// Twiddle tables exp(-j 2 pi k / 2^15), filled once per device at set-up.
+// Twiddle tables exp(-j 2 pi k / 2^15) in FP64, FP32 and double-float
+// {re.h, re.l, im.h, im.l}, filled once per device at set-up.
 static __device__ __align__(256) c128 g_tw64[1 << kMaxLog2L];
 static __device__ __align__(256) c64 g_tw32[1 << kMaxLog2L];
+static __device__ __align__(256) float4 g_twdf[1 << kMaxLog2L];
 // Instance descriptor and work counter of the launch.
 static __device__ __align__(16) InstDesc g_desc;
 static __device__ int g_counter;
@@ -46,6 +48,7 @@ struct DeviceSetup {
   void* scratch = nullptr;
   c128* tw64 = nullptr;
   c64* tw32 = nullptr;
+  float4* twdf = nullptr;
   InstDesc* desc = nullptr;
   int* counter = nullptr;
 };
@@ -53,14 +56,24 @@ struct DeviceSetup {
 std::mutex g_mu;
 DeviceSetup g_setup[kMaxDevices];
 
-__global__ void fill_twiddles(c128* t64, c64* t32) {
+__global__ void fill_twiddles(c128* t64, c64* t32, float4* tdf) {
   const int M = 1 << kMaxLog2L;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
     double s, c;
     sincospi(2.0 * (double)k / (double)M, &s, &c);
     t64[k] = mk(c, -s);
     t32[k] = mk((float)c, (float)-s);
+    const float ch = (float)c, sh = (float)-s;
+    tdf[k] = make_float4(ch, (float)(c - (double)ch), sh, (float)(-s - (double)sh));
   }
+}
+
+// The launch's instance descriptor, passed by value (a kernel parameter, so
+// no host buffer has to outlive the call), and the zeroed work counter.  The
+// device code names the static arrays directly.
+__global__ void prepare_launch(InstDesc d) {
+  g_desc = d;
+  g_counter = 0;
 }
 
 // The entry point has no context to keep a message in; the status code is
@@ -71,7 +84,11 @@ lse_status set_err(lse_status s, const char* msg) {
 }
 
 // Look up the device addresses of the static arrays on the current device and
-// fill its twiddle tables.  Runs once per device, on the first call there.
+// fill its twiddle tables.  Runs once per device, on the first call there;
+// it waits for the fill on that call's stream, so later calls on any stream
+// find the tables complete.  The addresses are those of the device's current
+// primary context: after cudaDeviceReset they are stale, and the entry point
+// is not meant to be used past a reset.
 lse_status setup(int dev, cudaStream_t st, DeviceSetup** out) {
   std::lock_guard<std::mutex> lock(g_mu);
   DeviceSetup& d = g_setup[dev];
@@ -79,11 +96,13 @@ lse_status setup(int dev, cudaStream_t st, DeviceSetup** out) {
     if (cudaGetSymbolAddress((void**)&d.scratch, g_scratch) != cudaSuccess ||
         cudaGetSymbolAddress((void**)&d.tw64, g_tw64) != cudaSuccess ||
         cudaGetSymbolAddress((void**)&d.tw32, g_tw32) != cudaSuccess ||
+        cudaGetSymbolAddress((void**)&d.twdf, g_twdf) != cudaSuccess ||
         cudaGetSymbolAddress((void**)&d.desc, g_desc) != cudaSuccess ||
         cudaGetSymbolAddress((void**)&d.counter, g_counter) != cudaSuccess)
       return set_err(LSE_ECUDA, "cudaGetSymbolAddress failed for the static scratch arrays");
-    fill_twiddles<<<64, 256, 0, st>>>(d.tw64, d.tw32);
-    if (cudaGetLastError() != cudaSuccess) return set_err(LSE_ECUDA, "twiddle set-up launch failed");
+    fill_twiddles<<<64, 256, 0, st>>>(d.tw64, d.tw32, d.twdf);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+      return set_err(LSE_ECUDA, "twiddle set-up failed");
     d.done = true;
   }
   *out = &d;
@@ -100,6 +119,9 @@ LSE_API lse_status lse_fit_noalloc_d(const lse_config* cfg, const float* y_d, in
   if (cfg) c = *cfg; else lse_config_default(&c);
   if (!y_d || !out) return set_err(LSE_EINVAL, "y_d and out must not be NULL");
   if (N < 2 || N > kMaxN) return set_err(LSE_EINVAL, "lse_fit_noalloc_d: N must be in [2, 4096]");
+  if (c.grid_size < 0) return set_err(LSE_EINVAL, "lse_fit_noalloc_d: grid_size must be >= 0");
+  if (c.flags & ~(uint64_t)(LSE_FLAG_NO_AUTOTUNE | LSE_FLAG_NO_CLUSTER))
+    return set_err(LSE_EINVAL, "lse_fit_noalloc_d: unknown flag bits");
   const int L = c.grid_size ? c.grid_size : 1 << (int)std::lround(std::log2(8.0 * N));
   if ((L & (L - 1)) || L < 2 * N || L > (1 << kMaxLog2L))
     return set_err(LSE_EINVAL, "lse_fit_noalloc_d: L must be a power of two with 2N <= L <= 32768");
@@ -118,13 +140,13 @@ LSE_API lse_status lse_fit_noalloc_d(const lse_config* cfg, const float* y_d, in
   lse_status s = setup(dev, st, &d);
   if (s != LSE_OK) return s;
   const InstDesc h{0, N, L, 0, 0, 0, 0};  // result slot 0
-  if (cudaMemcpyAsync(d->desc, &h, sizeof(h), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemsetAsync(d->counter, 0, sizeof(int), st) != cudaSuccess)
+  prepare_launch<<<1, 1, 0, st>>>(h);
+  if (cudaGetLastError() != cudaSuccess)
     return set_err(LSE_ECUDA, "lse_fit_noalloc_d: staging the launch descriptor failed");
   const FitConfig fc{c.tau, c.max_outer, c.max_inner, c.approx_activation_iters, !(c.flags & LSE_FLAG_NO_CLUSTER)};
   const FitOut fo{out->theta, out->gamma, (c128*)out->alpha, out->K, out->beta, out->objective, out->iters,
                   out->n_evals, out->n_grid, out->status};
-  const Tables tab{d->tw64, d->tw32, kMaxLog2L};
+  const Tables tab{d->tw64, d->tw32, kMaxLog2L, d->twdf};
   if (launch_fit(prec, y_d, d->desc, 1, N, L, fc, tab, fo, d->scratch, d->counter, 1, st) != cudaSuccess)
     return set_err(LSE_ECUDA, "lse_fit_noalloc_d: fit kernel launch failed");
   return LSE_OK;

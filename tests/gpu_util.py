@@ -38,3 +38,17 @@ def match_fit(gpu, ref):
         return 0.0
     d = wrapdist(gpu["theta"], ref.theta)
     return float(d.max())
+
+
+def s_fp32_bound(ev, L):
+    """Pointwise error bound of an FP32 grid s (the reading of the 1e-4 bar on
+    the FP32-grid paths): s(theta) = sum_{|i|<N} w(i) e^{j 2 pi i theta} with
+    w(i) = sum_{q-p=i} [C^{-1}]_{pq} (the lag sums of C^{-1}, App. B), and a
+    length-L FFT in FP32 gives each output to within about
+    (log2 L + 3) rounding errors of the running sums, each at most
+    u32 * sum_i |w(i)| (a complex operation contributes up to ~4 u32).  So
+    |s_gpu(l) - s(l)| <= 1e-4 s(l) + 4 (log2 L + 3) 2^-24 ||w||_1.
+    Returns the second term; ev is the oracle's DenseEval."""
+    Cinv = ev.solve(np.eye(ev.N, dtype=complex))
+    w1 = sum(abs(np.trace(Cinv, offset=i)) for i in range(-(ev.N - 1), ev.N))
+    return 4.0 * (np.log2(L) + 3.0) * 2.0 ** -24 * w1

@@ -80,3 +80,34 @@ def test_plan_and_graph_equal_direct_and_single(lse_mod, prec):
         K = int(d["K"][b])
         assert K == ref.K
         assert np.all(wrapdist(d["theta"][offs[b]:offs[b] + K], ref.theta) < 1e-6)
+
+
+def test_fit_batch_d_captured_in_cuda_graph(lse_mod):
+    """lse_fit_batch_d captured in a CUDA graph after one uncaptured call with
+    the same offsets replays to the direct call's results exactly."""
+    import torch
+    lse = lse_mod
+    insts = ragged(n=6, seed0=9400)
+    ys = [i.y for i in insts]
+    offs = np.concatenate([[0], np.cumsum([len(y) for y in ys])]).astype(np.int64)
+    y_d = torch.from_numpy(np.concatenate(ys)).cuda()
+    ctx = lse.lse_create(lse.lse_config_default(precision=lse.LSE_PREC_MIXED_DF))
+    try:
+        st = torch.cuda.Stream()
+        st.wait_stream(torch.cuda.current_stream())
+        direct = lse.alloc_batch_out(offs)
+        lse.lse_fit_batch_d(ctx, y_d, offs, direct, st)
+        st.synchronize()
+        graphed = lse.alloc_batch_out(offs)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st, capture_error_mode="thread_local"):
+            lse.lse_fit_batch_d(ctx, y_d, offs, graphed, st)
+        for _ in range(2):
+            for v in graphed.values():
+                v.zero_()
+            g.replay()
+            torch.cuda.synchronize()
+            for k in direct:
+                assert torch.equal(graphed[k], direct[k]), k
+    finally:
+        lse.lse_destroy(ctx)

@@ -11,7 +11,7 @@ import pytest
 
 from oracle import dense as dn
 from paper_1705_06073_gb300 import synth
-from tests.gpu_util import grid_errors
+from tests.gpu_util import grid_errors, s_fp32_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -57,12 +57,20 @@ def test_grid_fp64_matches_oracle(ctxs, N, K, L):
 @pytest.mark.parametrize("which", [1, 2])
 @pytest.mark.parametrize("N,K,L", CASES)
 def test_grid_mixed_matches_oracle(ctxs, N, K, L, which):
+    """FP32 spectra: 1e-4 normwise on every output, and s pointwise within
+    1e-4 s(l) plus the FP32 FFT's own error bound (tests.gpu_util.s_fp32_bound):
+    near a strong component s dips to ~1/gamma while the transform's rounding
+    error scales with the whole sequence, so a pure 1e-4 s(l) bound is out of
+    FP32's reach there."""
     from paper_1705_06073_gb300 import lse
     y, th, ga, be = state(N, K, 2000 + N)
     got = lse.lse_eval_grid(ctxs[which], y, th, ga, be, L, f64=False)
-    ref = dn.DenseEval(y, th, ga, be).grid(L, derivatives=True)
+    ev = dn.DenseEval(y, th, ga, be)
+    ref = ev.grid(L, derivatives=True)
     err = grid_errors(got, ref, N)
     assert max(err.values()) < 1e-4, err
+    bound = 1e-4 * ref["s"] + s_fp32_bound(ev, L)
+    assert np.all(np.abs(got["s"] - ref["s"]) <= bound), float(np.max(np.abs(got["s"] - ref["s"]) / bound))
 
 
 def test_grid_batch_ragged_device(ctxs):
@@ -109,3 +117,50 @@ def test_grid_rejects_bad_arguments(ctxs):
         lse.lse_eval_grid(ctxs[0], y, [], [], 0.0, 16, f64=True)  # beta <= 0
     with pytest.raises(lse.LseError):
         lse.lse_eval_grid(ctxs[0], y, [], [], 1.0, 16, f64=False)  # dtype mismatch
+
+
+@pytest.mark.parametrize("which", [0, 2])
+def test_grid_batch_captured_in_cuda_graph(ctxs, which):
+    """The factorisation and grid kernels of lse_eval_grid_batch_d captured in
+    a CUDA graph (after one uncaptured call of the same shapes) replay to the
+    direct call's outputs, bit for bit; the call itself does not wait for the
+    device (it returns while the kernels are still queued)."""
+    import torch
+    from paper_1705_06073_gb300 import lse
+    f64 = which == 0
+    specs = [(37, 2, 128), (128, 0, 256), (250, 6, 512), (64, 3, 512)]
+    ys, ths, gas, bes = [], [], [], []
+    for i, (N, K, L) in enumerate(specs):
+        y, th, ga, be = state(N, K, 3100 + i)
+        ys.append(y); ths.append(th); gas.append(ga); bes.append(be)
+    yo = np.concatenate([[0], np.cumsum([len(y) for y in ys])])
+    ko = np.concatenate([[0], np.cumsum([len(t) for t in ths])])
+    Ls = np.array([s[2] for s in specs], np.int32)
+    dev = torch.device("cuda:0")
+    y_d = torch.from_numpy(np.concatenate(ys)).to(dev)
+    th_d = torch.from_numpy(np.concatenate(ths + [np.zeros(1)])).to(dev)
+    ga_d = torch.from_numpy(np.concatenate(gas + [np.zeros(1)])).to(dev)
+    be_d = torch.tensor(bes, dtype=torch.float64, device=dev)
+    G = int(Ls.sum())
+    ct, rt = (torch.complex128, torch.float64) if f64 else (torch.complex64, torch.float32)
+
+    def alloc():
+        return {f: torch.zeros(G, dtype=ct if f in ("q", "dq", "d2q") else rt, device=dev) for f in FIELDS}
+
+    st = torch.cuda.Stream(device=dev)
+    st.wait_stream(torch.cuda.current_stream())
+    direct = alloc()
+    with torch.cuda.stream(st):
+        lse.lse_eval_grid_batch_d(ctxs[which], y_d, yo, th_d, ga_d, ko, be_d, Ls, direct, f64, stream=st)
+    st.synchronize()
+    graphed = alloc()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st, capture_error_mode="thread_local"):
+        lse.lse_eval_grid_batch_d(ctxs[which], y_d, yo, th_d, ga_d, ko, be_d, Ls, graphed, f64, stream=st)
+    for _ in range(2):
+        for v in graphed.values():
+            v.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for f in FIELDS:
+            assert torch.equal(graphed[f], direct[f]), f
