@@ -104,6 +104,16 @@ typedef struct lse_config {
  * inner products are summed in a different order). */
 #define LSE_FLAG_NO_CLUSTER 2u
 
+/* Run the O(N^2) Levinson-Durbin recursion for every N.  By default the
+ * Gohberg-Semencul generator of an instance with N >= 64 comes from a
+ * divide-and-conquer ("superfast") Schur recursion, O(N log^2 N): runs of
+ * orders combined as 2x2 polynomial matrices by FFT products (the faster
+ * route for large N the paper names, Sec. III intro), in one thread block per
+ * instance.  Both give the same generator, ln|C| and pivots to rounding; the
+ * superfast path loses about a decimal digit more to rounding at large
+ * kappa(C). */
+#define LSE_FLAG_LEVINSON 4u
+
 /* Fill cfg with the paper's defaults (device 0, FP64, tau = 5, ...). */
 LSE_API void lse_config_default(lse_config* cfg);
 

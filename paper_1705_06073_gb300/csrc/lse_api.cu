@@ -64,7 +64,7 @@ struct lse_ctx {
 
 struct lse_plan {
   lse_ctx* ctx = nullptr;
-  int B = 0, Nmax = 0, Lmax = 0, grid = 0, prec = 0;
+  int B = 0, Nmax = 0, Lmax = 0, Nmin = 0, grid = 0, prec = 0;
   DevBuf desc, counter, ws;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -256,7 +256,7 @@ void save_autotune(const lse_ctx* c) {
 // largest N first (longest-processing-time order) so that a ragged batch does
 // not end waiting on a big instance started last.  idx keeps the result slot.
 lse_status plan_fit_descs(lse_ctx* ctx, const int64_t* offsets, int32_t B, std::vector<InstDesc>& d, int& Nmax,
-                          int& Lmax) {
+                          int& Lmax, int* Nmin = nullptr) {
   if (B < 1 || !offsets) return fail(ctx, LSE_EINVAL, "null offsets or B < 1");
   if (offsets[0] != 0) return fail(ctx, LSE_EINVAL, "offsets[0] must be 0");
   d.resize(B);
@@ -273,6 +273,7 @@ lse_status plan_fit_descs(lse_ctx* ctx, const int64_t* offsets, int32_t B, std::
     Lmax = std::max(Lmax, L);
   }
   std::stable_sort(d.begin(), d.end(), [](const InstDesc& a, const InstDesc& b) { return a.N > b.N; });
+  if (Nmin) *Nmin = d.back().N;
   return LSE_OK;
 }
 
@@ -320,7 +321,7 @@ lse_status lse_create(const lse_config* cfg, lse_ctx** out) {
   if (c.precision != LSE_PREC_FP64 && c.precision != LSE_PREC_MIXED && c.precision != LSE_PREC_MIXED_DF)
     return LSE_EINVAL;
   if (c.max_outer < 1 || c.max_inner < 0 || c.approx_activation_iters < 0 || !(c.tau >= 0.0) ||
-      (c.flags & ~(uint64_t)(LSE_FLAG_NO_AUTOTUNE | LSE_FLAG_NO_CLUSTER)))
+      (c.flags & ~(uint64_t)(LSE_FLAG_NO_AUTOTUNE | LSE_FLAG_NO_CLUSTER | LSE_FLAG_LEVINSON)))
     return LSE_EINVAL;
   if (c.grid_size < 0 || (c.grid_size > 0 && !is_pow2(c.grid_size))) return LSE_EINVAL;
   int ndev = 0;
@@ -388,8 +389,8 @@ lse_status lse_fit_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* offset
   cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
   const bool cap = is_capturing(st);
   std::vector<InstDesc> d;
-  int Nmax = 0, Lmax = 0;
-  lse_status s = plan_fit_descs(ctx, offsets, B, d, Nmax, Lmax);
+  int Nmax = 0, Lmax = 0, Nmin = 0;
+  lse_status s = plan_fit_descs(ctx, offsets, B, d, Nmax, Lmax, &Nmin);
   if (s) return s;
   const int prec = ctx->cfg.precision;
   const int log2t = std::max(ilog2((uint32_t)Lmax), ilog2(2u * (uint32_t)Nmax));
@@ -403,7 +404,7 @@ lse_status lse_fit_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* offset
   if ((s = stage(ctx, ctx->fit_meta, d.data(), d.size() * sizeof(InstDesc), st, cap))) return s;
   LSE_CUDA(ctx, cudaMemsetAsync(ctx->counter.p, 0, sizeof(int), st));
   FitConfig fc{ctx->cfg.tau, ctx->cfg.max_outer, ctx->cfg.max_inner, ctx->cfg.approx_activation_iters,
-               !(ctx->cfg.flags & LSE_FLAG_NO_CLUSTER)};
+               !(ctx->cfg.flags & LSE_FLAG_NO_CLUSTER), superfast_min_n(ctx->cfg.flags), Nmin};
   FitOut fo{out->theta, out->gamma, (c128*)out->alpha, out->K, out->beta, out->objective, out->iters,
             out->n_evals, out->n_grid, out->status};
   record(ctx, 0, st, true);
@@ -421,8 +422,8 @@ lse_status lse_plan_fit(lse_ctx* ctx, const int64_t* offsets, int32_t B, lse_pla
   *out = nullptr;
   cudaSetDevice(ctx->cfg.device);
   std::vector<InstDesc> d;
-  int Nmax = 0, Lmax = 0;
-  lse_status s = plan_fit_descs(ctx, offsets, B, d, Nmax, Lmax);
+  int Nmax = 0, Lmax = 0, Nmin = 0;
+  lse_status s = plan_fit_descs(ctx, offsets, B, d, Nmax, Lmax, &Nmin);
   if (s) return s;
   if ((s = ensure_tables(ctx, std::max(ilog2((uint32_t)Lmax), ilog2(2u * (uint32_t)Nmax))))) return s;
   lse_plan* p = new lse_plan();
@@ -430,6 +431,7 @@ lse_status lse_plan_fit(lse_ctx* ctx, const int64_t* offsets, int32_t B, lse_pla
   p->B = B;
   p->Nmax = Nmax;
   p->Lmax = Lmax;
+  p->Nmin = Nmin;
   p->prec = ctx->cfg.precision;
   p->grid = std::min(B, ctx->sm_count);
   if ((s = ensure(ctx, p->desc, d.size() * sizeof(InstDesc))) || (s = ensure(ctx, p->counter, 256)) ||
@@ -451,7 +453,7 @@ lse_status lse_plan_launch(lse_plan* p, const float* y_d, const lse_batch_out* o
   cudaStream_t st = (cudaStream_t)stream;
   LSE_CUDA(ctx, cudaMemsetAsync(p->counter.p, 0, sizeof(int), st));
   const FitConfig fc{ctx->cfg.tau, ctx->cfg.max_outer, ctx->cfg.max_inner, ctx->cfg.approx_activation_iters,
-               !(ctx->cfg.flags & LSE_FLAG_NO_CLUSTER)};
+                     !(ctx->cfg.flags & LSE_FLAG_NO_CLUSTER), superfast_min_n(ctx->cfg.flags), p->Nmin};
   const FitOut fo{out->theta, out->gamma, (c128*)out->alpha, out->K, out->beta, out->objective, out->iters,
                   out->n_evals, out->n_grid, out->status};
   const cudaError_t e = launch_fit(p->prec, y_d, (const InstDesc*)p->desc.p, p->B, p->Nmax, p->Lmax, fc, tables(ctx),
@@ -607,7 +609,10 @@ lse_status lse_eval_grid_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* 
   lse_status sst = ensure_tables(ctx, log2t);
   if (sst) return sst;
   const int64_t totN = y_offsets[B];
-  const size_t fws = factor_workspace_bytes(Nmax) * B;
+  const int sfmin = superfast_min_n(ctx->cfg.flags);
+  int Nmin = Nmax;
+  for (int b = 0; b < B; ++b) Nmin = std::min(Nmin, d[b].N);
+  const size_t fws = factor_workspace_bytes(Nmax, sfmin) * B;
   const size_t gws = grid_workspace_bytes(B, g, f32);
   const size_t fac_bytes =
       (size_t)totN * (4 * sizeof(c128) + 3 * sizeof(c64)) + (size_t)B * (sizeof(double) + sizeof(int)) + 1024;
@@ -642,7 +647,8 @@ lse_status lse_eval_grid_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* 
   c64* omega32 = (c64*)(((uintptr_t)(status + B) + 255) & ~(uintptr_t)255);
   c64* x32 = omega32 + 2 * totN;
   record(ctx, 1, st, true);
-  cudaError_t e = launch_factor(ctx->cfg.precision == LSE_PREC_MIXED_DF, y_d, desc_d, B, Nmax, theta_d, gamma_d, beta_d,
+  cudaError_t e = launch_factor(ctx->cfg.precision == LSE_PREC_MIXED_DF, sfmin, Nmin, y_d, desc_d, B, Nmax, theta_d,
+                                gamma_d, beta_d,
                                 tables(ctx), ctx->ws.p, rho, x, omega, omega32, x32, delta, status,
                                 !(ctx->cfg.flags & LSE_FLAG_NO_CLUSTER), st);
   record(ctx, 1, st, false);

@@ -30,9 +30,11 @@
 //    the objective changes by less than N 1e-7 over an outer iteration.
 #include <cfloat>
 
+#include "../../include/lse.h"
 #include "lse_device.cuh"
 #include "lse_df64.cuh"
 #include "lse_internal.h"
+#include "lse_schur.cuh"
 
 namespace lse {
 
@@ -48,6 +50,8 @@ constexpr double kEpsL = 2.220446049250313e-16;
 constexpr int kST_OK = 0, kST_NUMERIC = 4, kST_NOTCONV = 5;
 // blocks per cluster for recursions too large for shared memory
 constexpr int kBigCluster = 8;
+// smallest N that uses the superfast Schur recursion by default
+constexpr int kSuperfastMinN = 64;
 
 // whether the recursion's c and a (2N complex doubles) and the first-column
 // tables fit in the block's dynamic shared memory
@@ -65,6 +69,8 @@ struct FitShared {
   double dred[kNT / 32];
   LevShared lev;
   LevCmd cmd;  // cluster mode: request from the first block (lev_send_cmd)
+  int sf_bad;  // superfast recursion: a pivot <= 0 or not finite
+  int sf_rex[kNT / 32];
   // instance state (written by thread 0, read by all after a barrier)
   int inst, K, status, n_evals, n_grid, cand_count, flag;
   double beta, zeta, eps_beta, tau;
@@ -92,6 +98,7 @@ struct Work {
   c128* cand_q;     // Lmax
   double* rs_theta;  // kRescore: frequencies being re-scored
   c128* rs_sums;     // 7 * kRescore
+  float4* sf;        // superfast Schur recursion (schur_workspace_elems(Nmax))
 };
 
 constexpr int kRescore = 1024;  // grid points re-scored in FP64 per batch
@@ -123,6 +130,7 @@ __host__ __device__ inline Layout make_layout(int Nmax, int Lmax) {
   put(sizeof(c128) * (size_t)Lmax);                                     // cand_q
   put(sizeof(double) * (size_t)kRescore);                               // rs_theta
   put(sizeof(c128) * 7 * (size_t)kRescore);                             // rs_sums
+  put(sizeof(float4) * schur_workspace_elems(Nmax));                     // sf
   L.total = o;
   return L;
 }
@@ -157,6 +165,7 @@ __device__ Work<TG> carve(char* base, int Nmax, int Lmax) {
   w.cand_q = (c128*)(base + L.off[i++]);
   w.rs_theta = (double*)(base + L.off[i++]);
   w.rs_sums = (c128*)(base + L.off[i++]);
+  w.sf = (float4*)(base + L.off[i++]);
   return w;
 }
 
@@ -202,6 +211,8 @@ struct Fitter {
   int N, L, log2L, log2M2;
   bool lev_smem;
   c128 *lev_c, *lev_a, *tables;
+  float4* sf_smem;  // superfast recursion: its shared-memory part (after the tables)
+  int sf_lsm;
   Twiddles<double> tw64;
   Twiddles<TG> twg;
 
@@ -214,7 +225,14 @@ struct Fitter {
     if constexpr (PREC == 2) block_first_column_df<kNT>(lev_c, th, ga, K, beta, N, tables);
     else block_first_column<kNT>(lev_c, th, ga, K, beta, N, tables);
     LevResult lr;
-    if constexpr (PREC == 2) {
+    if (superfast()) {
+      if constexpr (PREC == 2)
+        lr = block_superfast<kNT>(PolDF{A->tab.twdf, A->tab.log2max}, lev_c, lev_a, N, w.sf, sf_smem, sf_lsm,
+                                  &sh->sf_bad, sh->dred, sh->sf_rex);
+      else
+        lr = block_superfast<kNT>(Pol64{A->tab.tw64, A->tab.log2max}, lev_c, lev_a, N, w.sf, sf_smem, sf_lsm,
+                                  &sh->sf_bad, sh->dred, sh->sf_rex);
+    } else if constexpr (PREC == 2) {
       if (A->cluster == 2 && lev_smem) lr = cluster_levinson();
       else if (A->cluster == kBigCluster && !lev_smem) lr = cluster_levinson_big();
       else lr = block_levinson_df<kNT>(lev_c, lev_a, N, (float4*)sh->red, &sh->lev);
@@ -258,6 +276,14 @@ struct Fitter {
     }
     if (want_sums && K > 0) compute_sums(th, K);
     return 0;
+  }
+
+  // the superfast Schur recursion (lse_schur.cuh) for this instance?  On the
+  // double-float path it needs the double-float twiddle table.
+  __device__ bool superfast() const {
+    if (A->cfg.sf_min_n <= 0 || N < A->cfg.sf_min_n) return false;
+    if constexpr (PREC == 2) return A->tab.twdf != nullptr;
+    return true;
   }
 
   // The recursion shared with the second block of the cluster: convert c,
@@ -670,8 +696,11 @@ struct Fitter {
       part += norm2(v);
     }
     const double yy = block_sum<kNT>(part, sh->dred);
-    // Levinson arrays in shared memory when they fit
-    lev_smem = lev_in_smem(N);
+    // Levinson arrays in shared memory when they fit and the Levinson
+    // recursion runs; the superfast recursion uses the shared memory after
+    // the first-column tables for its short runs instead
+    const bool sf = superfast();
+    lev_smem = !sf && lev_in_smem(N);
     if (lev_smem) {
       lev_c = (c128*)dsm;
       lev_a = lev_c + N;
@@ -680,6 +709,13 @@ struct Fitter {
       lev_c = w.c;
       lev_a = w.a;
       tables = (c128*)dsm;
+    }
+    {
+      int S, H;
+      first_column_split(N, S, H);
+      const size_t tb = (sizeof(c128) * kFirstColumnChunk * (S + H) + 255) & ~size_t(255);
+      sf_smem = reinterpret_cast<float4*>(dsm + tb);
+      sf_lsm = schur_pick_lsm(kSmemBytes - tb);
     }
     if (threadIdx.x == 0) {
       sh->yy = yy;
@@ -866,6 +902,8 @@ __global__ void __launch_bounds__(threads_for<PREC>(), 1) fit_kernel(FitArgs arg
 
 }  // namespace
 
+int superfast_min_n(uint64_t flags) { return (flags & LSE_FLAG_LEVINSON) ? 0 : kSuperfastMinN; }
+
 size_t fit_workspace_bytes(int Nmax, int Lmax, int prec) {
   return prec ? make_layout<float>(Nmax, Lmax).total : make_layout<double>(Nmax, Lmax).total;
 }
@@ -915,7 +953,9 @@ cudaError_t launch_fit(int prec, const float* y, const InstDesc* inst, int B, in
   // sharing the recursions of the instances too large for shared memory
   // through global memory, when the batch leaves kBigCluster SMs per instance.
   a.cluster = 0;
-  if (prec == 2 && cfg.cluster) {
+  // no clusters when every instance runs the superfast recursion in one block
+  const bool any_levinson = cfg.sf_min_n <= 0 || cfg.Nmin < cfg.sf_min_n || (prec == 2 && !tab.twdf);
+  if (prec == 2 && cfg.cluster && any_levinson) {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {

@@ -21,6 +21,7 @@
 #include "lse_df64.cuh"
 #include "lse_fft_smem.cuh"
 #include "lse_internal.h"
+#include "lse_schur.cuh"
 
 namespace lse {
 
@@ -31,9 +32,10 @@ template <bool DF>
 __host__ __device__ constexpr int factor_threads() { return 256; }
 
 struct FactorLayout {
-  size_t y, c, a, Yf, buf, total, M2;
+  size_t y, c, a, Yf, buf, sf, total, M2;
 };
-__host__ __device__ inline FactorLayout factor_layout(int Nmax) {
+// sf: whether some instance runs the superfast recursion (its workspace)
+__host__ __device__ inline FactorLayout factor_layout(int Nmax, bool sf) {
   FactorLayout L;
   const size_t M2 = (size_t)1 << ilog2(2u * (uint32_t)Nmax);
   size_t o = 0;
@@ -43,6 +45,7 @@ __host__ __device__ inline FactorLayout factor_layout(int Nmax) {
   L.a = put(sizeof(c128) * Nmax);
   L.Yf = put(sizeof(c128) * M2);
   L.buf = put(sizeof(c128) * M2 * 5);
+  L.sf = put(sf ? sizeof(float4) * schur_workspace_elems(Nmax) : 0);
   L.total = o;
   L.M2 = M2;
   return L;
@@ -59,11 +62,15 @@ template <bool DF>
 __global__ void __launch_bounds__(factor_threads<DF>(), 1)
     factor_kernel(const float* y, const InstDesc* inst, int Nmax, const double* theta, const double* gamma,
                   const double* beta, Tables tab, char* ws, size_t ws_bytes, c128* rho_out, c128* x_out,
-                  c128* omega_out, c64* omega32_out, c64* x32_out, double* delta_out, int* status, int csize) {
+                  c128* omega_out, c64* omega32_out, c64* x32_out, double* delta_out, int* status, int csize,
+                  int sf_min_n) {
   constexpr int kFNT = factor_threads<DF>();
   __shared__ c128 red[kFNT];
   __shared__ LevShared lev;
   __shared__ LevCmd cmd;
+  __shared__ int sf_bad;
+  __shared__ double sf_red[kFNT / 32];
+  __shared__ int sf_rex[kFNT / 32];
   extern __shared__ __align__(16) char dsm[];
   int b = blockIdx.x;
   if constexpr (DF) {
@@ -91,7 +98,10 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
   const InstDesc d = inst[b];
   const int N = d.N;
   char* base = ws + (size_t)b * ws_bytes;
-  const FactorLayout FL = factor_layout(Nmax);
+  const FactorLayout FL = factor_layout(Nmax, sf_min_n > 0 && Nmax >= sf_min_n);
+  // the superfast Schur recursion (lse_schur.cuh) for this instance?
+  bool sf = sf_min_n > 0 && N >= sf_min_n;
+  if constexpr (DF) sf = sf && tab.twdf != nullptr;
   c128* yv = (c128*)(base + FL.y);
   c128* Yf = (c128*)(base + FL.Yf);
   c128* bufp = (c128*)(base + FL.buf);
@@ -107,7 +117,7 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
   const size_t tab_bytes = sizeof(c128) * kFirstColumnChunk * (S + H);
   const int smem_cap = 200 * 1024;
   c128 *cc, *aa, *tables;
-  if (2 * sizeof(c128) * (size_t)N + tab_bytes <= (size_t)smem_cap) {
+  if (!sf && 2 * sizeof(c128) * (size_t)N + tab_bytes <= (size_t)smem_cap) {
     cc = (c128*)dsm; aa = cc + N; tables = aa + N;
   } else {
     cc = (c128*)(base + FL.c); aa = (c128*)(base + FL.a); tables = (c128*)dsm;
@@ -115,7 +125,21 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
   if constexpr (DF) block_first_column_df<kFNT>(cc, theta + d.k_off, gamma + d.k_off, d.K, beta[b], N, tables);
   else block_first_column<kFNT>(cc, theta + d.k_off, gamma + d.k_off, d.K, beta[b], N, tables);
   LevResult lr;
-  if constexpr (DF) {
+  if (sf) {
+    // a cluster launch still owes its other blocks their release
+    if (DF && csize > 1) {
+      if (threadIdx.x == 0) lev_send_cmd(&cmd, csize, LevCmd{0, N, 0.0, cc, aa});
+      cluster_barrier();
+    }
+    float4* sfw = (float4*)(base + FL.sf);
+    const size_t tb = (tab_bytes + 255) & ~size_t(255);
+    float4* sfs = reinterpret_cast<float4*>(dsm + tb);
+    const int lsm = schur_pick_lsm(smem_cap - tb);
+    if constexpr (DF)
+      lr = block_superfast<kFNT>(PolDF{tab.twdf, tab.log2max}, cc, aa, N, sfw, sfs, lsm, &sf_bad, sf_red, sf_rex);
+    else
+      lr = block_superfast<kFNT>(Pol64{tab.tw64, tab.log2max}, cc, aa, N, sfw, sfs, lsm, &sf_bad, sf_red, sf_rex);
+  } else if constexpr (DF) {
     if (csize > 1) {
       // exactly one request per launch: the shared recursion, or a release
       const bool in_smem = cc == (c128*)dsm;
@@ -372,10 +396,13 @@ __global__ void __launch_bounds__(NT)
 
 }  // namespace
 
-size_t factor_workspace_bytes(int Nmax) { return factor_layout(Nmax).total; }
+size_t factor_workspace_bytes(int Nmax, int sf_min_n) {
+  return factor_layout(Nmax, sf_min_n > 0 && Nmax >= sf_min_n).total;
+}
 
 template <bool DF>
-static cudaError_t launch_factor_t(const float* y, const InstDesc* inst, int B, int Nmax, const double* theta,
+static cudaError_t launch_factor_t(int sf_min_n, int Nmin, const float* y, const InstDesc* inst, int B, int Nmax,
+                                   const double* theta,
                                    const double* gamma, const double* beta, const Tables& tab, void* ws,
                                    c128* rho_out, c128* x_out, c128* omega_out, c64* omega32_out, c64* x32_out,
                                    double* delta_out, int* status, bool allow_cluster, cudaStream_t stream) {
@@ -387,7 +414,9 @@ static cudaError_t launch_factor_t(const float* y, const InstDesc* inst, int B, 
   // kFactorCluster blocks when some recursion is too large for shared memory
   // and the launch leaves the SMs for them
   int csize = 1;
-  if (DF && allow_cluster) {
+  // clusters serve the Levinson recursion only
+  const bool any_levinson = sf_min_n <= 0 || Nmin < sf_min_n || !tab.twdf;
+  if (DF && allow_cluster && any_levinson) {
     int S, H;
     first_column_split(Nmax, S, H);
     const size_t need = 2 * sizeof(c128) * (size_t)Nmax + sizeof(c128) * kFirstColumnChunk * (S + H);
@@ -401,7 +430,7 @@ static cudaError_t launch_factor_t(const float* y, const InstDesc* inst, int B, 
       }
     }
   }
-  const size_t wsb = factor_workspace_bytes(Nmax);
+  const size_t wsb = factor_workspace_bytes(Nmax, sf_min_n);
   if (csize > 1) {
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(csize * B);
@@ -416,22 +445,22 @@ static cudaError_t launch_factor_t(const float* y, const InstDesc* inst, int B, 
     lc.attrs = at;
     lc.numAttrs = 1;
     return cudaLaunchKernelEx(&lc, factor_kernel<DF>, y, inst, Nmax, theta, gamma, beta, tab, (char*)ws, wsb, rho_out,
-                              x_out, omega_out, omega32_out, x32_out, delta_out, status, csize);
+                              x_out, omega_out, omega32_out, x32_out, delta_out, status, csize, sf_min_n);
   }
   factor_kernel<DF><<<B, factor_threads<DF>(), smem, stream>>>(y, inst, Nmax, theta, gamma, beta, tab, (char*)ws, wsb,
                                                                rho_out, x_out, omega_out, omega32_out, x32_out,
-                                                               delta_out, status, 1);
+                                                               delta_out, status, 1, sf_min_n);
   return cudaGetLastError();
 }
 
-cudaError_t launch_factor(bool df, const float* y, const InstDesc* inst, int B, int Nmax, const double* theta,
-                          const double* gamma, const double* beta, const Tables& tab, void* ws, c128* rho_out,
-                          c128* x_out, c128* omega_out, c64* omega32_out, c64* x32_out, double* delta_out,
-                          int* status, bool allow_cluster, cudaStream_t stream) {
-  return df ? launch_factor_t<true>(y, inst, B, Nmax, theta, gamma, beta, tab, ws, rho_out, x_out, omega_out,
-                                    omega32_out, x32_out, delta_out, status, allow_cluster, stream)
-            : launch_factor_t<false>(y, inst, B, Nmax, theta, gamma, beta, tab, ws, rho_out, x_out, omega_out,
-                                     omega32_out, x32_out, delta_out, status, false, stream);
+cudaError_t launch_factor(bool df, int sf_min_n, int Nmin, const float* y, const InstDesc* inst, int B, int Nmax,
+                          const double* theta, const double* gamma, const double* beta, const Tables& tab, void* ws,
+                          c128* rho_out, c128* x_out, c128* omega_out, c64* omega32_out, c64* x32_out,
+                          double* delta_out, int* status, bool allow_cluster, cudaStream_t stream) {
+  return df ? launch_factor_t<true>(sf_min_n, Nmin, y, inst, B, Nmax, theta, gamma, beta, tab, ws, rho_out, x_out,
+                                    omega_out, omega32_out, x32_out, delta_out, status, allow_cluster, stream)
+            : launch_factor_t<false>(sf_min_n, Nmin, y, inst, B, Nmax, theta, gamma, beta, tab, ws, rho_out, x_out,
+                                     omega_out, omega32_out, x32_out, delta_out, status, false, stream);
 }
 
 size_t grid_workspace_bytes(int B, int64_t total_L, bool f32) {

@@ -28,8 +28,14 @@ struct InstDesc {
 struct FitConfig {
   double tau;
   int max_outer, max_inner, approx_iters;
-  int cluster;  // clusters of two blocks allowed (double-float path)
+  int cluster;    // thread-block clusters allowed for the Levinson recursion (double-float path)
+  int sf_min_n;   // instances with N >= sf_min_n use the superfast Schur recursion (0: none)
+  int Nmin;       // smallest N of the launch
 };
+
+// Smallest N for which the superfast Schur recursion replaces the Levinson
+// recursion, given the lse_config flags (LSE_FLAG_LEVINSON: never).
+int superfast_min_n(uint64_t flags);
 
 // Device outputs of the fit kernel (see lse_batch_out).
 struct FitOut {
@@ -65,8 +71,9 @@ cudaError_t launch_fit(int prec, const float* y, const InstDesc* inst, int B, in
                        const Tables& tab, const FitOut& out, void* ws, int* counter, int grid, cudaStream_t stream);
 
 // Eval-grid: per-instance factorisation (first column, Levinson, GS apply).
-size_t factor_workspace_bytes(int Nmax);
-cudaError_t launch_factor(bool df, const float* y, const InstDesc* inst, int B, int Nmax, const double* theta,
+size_t factor_workspace_bytes(int Nmax, int sf_min_n);
+cudaError_t launch_factor(bool df, int sf_min_n, int Nmin, const float* y, const InstDesc* inst, int B, int Nmax,
+                          const double* theta,
                           const double* gamma, const double* beta, const Tables& tab, void* ws, c128* rho_out,
                           c128* x_out, c128* omega_out, c64* omega32_out, c64* x32_out, double* delta_out,
                           int* status, bool allow_cluster, cudaStream_t stream);

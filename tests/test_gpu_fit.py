@@ -121,17 +121,19 @@ def test_fit_capacity_error(lse_mod):
 
 
 def test_cluster_recursion_matches_one_block():
-    """Double-float path: the same batch fitted with clusters of two blocks
-    (default for a batch smaller than half the SMs) and with one block per
-    instance (LSE_FLAG_NO_CLUSTER) gives the same fits to rounding: the two
-    differ only in the order the inner products of the recursion are summed."""
+    """Double-float path with the Levinson recursion (LSE_FLAG_LEVINSON): the
+    same batch fitted with clusters of two blocks (the default for a batch
+    smaller than half the SMs) and with one block per instance
+    (LSE_FLAG_NO_CLUSTER) gives the same fits to rounding: the two differ only
+    in the order the inner products of the recursion are summed."""
     from paper_1705_06073_gb300 import build, lse
     build.build()
     specs = [(256, 8), (1000, 16), (2048, 32), (4096, 64), (37, 2), (600, 9), (3000, 40), (5000, 70)]
     insts = [synth.make_instance(N, K, 20.0, 8100 + i) for i, (N, K) in enumerate(specs)]
     res = {}
     for flags in (0, lse.LSE_FLAG_NO_CLUSTER):
-        ctx = lse.lse_create(lse.lse_config_default(precision=lse.LSE_PREC_MIXED_DF, flags=flags))
+        ctx = lse.lse_create(lse.lse_config_default(precision=lse.LSE_PREC_MIXED_DF,
+                                                    flags=flags | lse.LSE_FLAG_LEVINSON))
         try:
             res[flags] = lse.lse_fit_batch(ctx, [i.y for i in insts])
         finally:
@@ -146,15 +148,17 @@ def test_cluster_recursion_matches_one_block():
 
 
 def test_big_cluster_recursion_matches_one_block():
-    """Double-float path, instances too large for the shared-memory recursion:
-    a small batch runs each recursion on a cluster of eight blocks sharing c
-    and a in global memory; the fits equal the one-block fits to rounding."""
+    """Double-float Levinson path, instances too large for the shared-memory
+    recursion: a small batch runs each recursion on a cluster of eight blocks
+    sharing c and a in global memory; the fits equal the one-block fits to
+    rounding."""
     from paper_1705_06073_gb300 import build, lse
     build.build()
     insts = [synth.make_instance(N, K, 20.0, 8200 + i) for i, (N, K) in enumerate([(8192, 64), (6500, 40)])]
     res = {}
     for flags in (0, lse.LSE_FLAG_NO_CLUSTER):
-        ctx = lse.lse_create(lse.lse_config_default(precision=lse.LSE_PREC_MIXED_DF, flags=flags))
+        ctx = lse.lse_create(lse.lse_config_default(precision=lse.LSE_PREC_MIXED_DF,
+                                                    flags=flags | lse.LSE_FLAG_LEVINSON))
         try:
             res[flags] = lse.lse_fit_batch(ctx, [i.y for i in insts])
         finally:
@@ -166,3 +170,53 @@ def test_big_cluster_recursion_matches_one_block():
             assert np.all(wrapdist(a["theta"], b["theta"]) < 1e-9)
             assert np.allclose(a["gamma"], b["gamma"], rtol=1e-8)
         assert abs(a["beta"] - b["beta"]) <= 1e-9 * b["beta"]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_levinson_path_matches_oracle(lse_mod, prec):
+    """The O(N^2) Levinson recursion (LSE_FLAG_LEVINSON) against the oracle's
+    fits: the N = 256 instance and a ragged batch of small instances."""
+    lse = lse_mod
+    inst, L = synth.single_n256()[0]
+    ctx = make_ctx(lse, L, precision=prec_of(lse, prec), flags=lse.LSE_FLAG_LEVINSON)
+    try:
+        gpu = lse.lse_fit(ctx, inst.y)
+    finally:
+        lse.lse_destroy(ctx)
+    ref = ofit.fit(inst.y, L)
+    check(gpu, ref)
+    assert gpu["n_evals"] == ref.n_evals
+    insts = [synth.make_instance(N, K, snr, 8300 + i) for i, (N, K, snr) in
+             enumerate([(100, 4, 15.0), (128, 10, 20.0), (300, 6, 25.0)])]
+    ctx = make_ctx(lse, 0, precision=prec_of(lse, prec), flags=lse.LSE_FLAG_LEVINSON)
+    try:
+        res = lse.lse_fit_batch(ctx, [i.y for i in insts])
+    finally:
+        lse.lse_destroy(ctx)
+    for g, i in zip(res, insts):
+        check(g, ofit.fit(i.y, synth.default_grid_size(len(i.y))))
+
+
+def test_superfast_matches_levinson():
+    """The superfast Schur recursion (default) and the Levinson recursion give
+    the same fits: equal K and evaluation counts, frequencies within 1e-8
+    cycles, on instances where the superfast recursion runs several levels of
+    merges (N up to 8192, 10-30 dB)."""
+    from paper_1705_06073_gb300 import build, lse
+    build.build()
+    specs = [(64, 3, 25.0), (1000, 16, 30.0), (4096, 64, 10.0), (4096, 64, 30.0), (8192, 64, 20.0), (3001, 40, 15.0)]
+    insts = [synth.make_instance(N, K, snr, 8400 + i) for i, (N, K, snr) in enumerate(specs)]
+    res = {}
+    for flags in (0, lse.LSE_FLAG_LEVINSON | lse.LSE_FLAG_NO_CLUSTER):
+        ctx = lse.lse_create(lse.lse_config_default(precision=lse.LSE_PREC_MIXED_DF, flags=flags))
+        try:
+            res[flags] = lse.lse_fit_batch(ctx, [i.y for i in insts])
+        finally:
+            lse.lse_destroy(ctx)
+    for a, b in zip(res[0], res[lse.LSE_FLAG_LEVINSON | lse.LSE_FLAG_NO_CLUSTER]):
+        assert a["status"] == b["status"] and a["status"] in (0, lse.LSE_ENOTCONV)
+        assert a["K"] == b["K"] and a["n_evals"] == b["n_evals"]
+        if a["K"]:
+            assert np.all(wrapdist(a["theta"], b["theta"]) < 1e-8)
+            assert np.allclose(a["gamma"], b["gamma"], rtol=1e-6)
+        assert abs(a["beta"] - b["beta"]) <= 1e-8 * b["beta"]

@@ -163,21 +163,25 @@ def test_max_size_grid_single_sinusoid_closed_form(lse_mod, prec):
 
 
 def test_big_cluster_factorisation_matches_one_block(lse_mod):
-    """Double-float eval-grid at N = 65536 (the recursion too large for shared
-    memory; a single instance runs it on a cluster of eight blocks through
-    global memory) against the same evaluation with one block
-    (LSE_FLAG_NO_CLUSTER): the grids agree to the FP32 output precision."""
+    """Double-float eval-grid at N = 65536 with the Levinson recursion
+    (LSE_FLAG_LEVINSON; too large for shared memory, a single instance runs it
+    on a cluster of eight blocks through global memory) against the same
+    evaluation with one block (LSE_FLAG_NO_CLUSTER), and against the default
+    superfast recursion: the grids agree to the FP32 output precision."""
     lse = lse_mod
     inst = synth.single_n65536()[0][0]
     N, L = inst.N, 2 * inst.N
     th = inst.theta
     ga = np.abs(inst.alpha) ** 2
     got = {}
-    for flags in (0, lse.LSE_FLAG_NO_CLUSTER):
+    lev = lse.LSE_FLAG_LEVINSON
+    for flags in (lev, lev | lse.LSE_FLAG_NO_CLUSTER, 0):
         ctx = lse.lse_create(lse.lse_config_default(precision=lse.LSE_PREC_MIXED_DF, flags=flags))
         try:
             got[flags] = lse.lse_eval_grid(ctx, inst.y, th, ga, inst.beta, L, f64=False)
         finally:
             lse.lse_destroy(ctx)
-    err = grid_errors(got[0], got[lse.LSE_FLAG_NO_CLUSTER], N)
+    err = grid_errors(got[lev], got[lev | lse.LSE_FLAG_NO_CLUSTER], N)
+    assert max(err.values()) < 1e-5, err
+    err = grid_errors(got[0], got[lev | lse.LSE_FLAG_NO_CLUSTER], N)
     assert max(err.values()) < 1e-5, err
