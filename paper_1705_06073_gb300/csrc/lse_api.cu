@@ -612,33 +612,33 @@ lse_status lse_eval_grid_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* 
   const int sfmin = superfast_min_n(ctx->cfg.flags);
   int Nmin = Nmax;
   for (int b = 0; b < B; ++b) Nmin = std::min(Nmin, d[b].N);
+  // grid tasks: on-chip ones first, then four-step ones with their offsets
+  std::vector<int4> tasks(5 * (size_t)B);
+  int n_small = 0;
+  size_t g4_elems = 0;
+  const int ntasks = grid_tasks(d.data(), B, f32, q, dq, d2q, s, ds, d2s, tasks.data(), &n_small, &g4_elems);
+  const int n_large = ntasks - n_small;
+  int Lmax_small = 0, Lmax_large = 0;
+  for (int b = 0; b < B; ++b) {
+    if (grid_on_chip(f32, d[b].L)) Lmax_small = std::max(Lmax_small, d[b].L);
+    else Lmax_large = std::max(Lmax_large, d[b].L);
+  }
   const size_t fws = factor_workspace_bytes(Nmax, sfmin) * B;
-  const size_t gws = grid_workspace_bytes(B, g, f32);
+  const size_t gws = grid_workspace_bytes(g4_elems, f32);
   const size_t fac_bytes =
       (size_t)totN * (4 * sizeof(c128) + 3 * sizeof(c64)) + (size_t)B * (sizeof(double) + sizeof(int)) + 1024;
   if ((sst = ensure(ctx, ctx->ws, std::max(fws, gws), cap))) return sst;
   if ((sst = ensure(ctx, ctx->fac, fac_bytes, cap))) return sst;
-  // launch metadata, one block: descriptors | grid workspace offsets (bytes
-  // from the workspace base, global-memory grid kernel) | on-chip task list
-  std::vector<int4> tasks(5 * (size_t)B);
-  const int ntasks = grid_tasks(d.data(), B, q, dq, d2q, s, ds, d2s, tasks.data());
+  // launch metadata, one block: descriptors | grid task list
   const size_t desc_b = ((size_t)B * sizeof(InstDesc) + 15) & ~size_t(15);
-  const size_t woff_b = ((size_t)B * sizeof(int64_t) + 15) & ~size_t(15);
-  std::vector<char> meta(desc_b + woff_b + (size_t)ntasks * sizeof(int4), 0);
+  std::vector<char> meta(desc_b + (size_t)std::max(ntasks, 1) * sizeof(int4), 0);
   std::memcpy(meta.data(), d.data(), (size_t)B * sizeof(InstDesc));
-  {
-    int64_t* woff = reinterpret_cast<int64_t*>(meta.data() + desc_b);
-    size_t o = 0;
-    const size_t es = f32 ? sizeof(c64) : sizeof(c128);
-    for (int b = 0; b < B; ++b) { woff[b] = (int64_t)o; o += (size_t)L[b] * 2 * 5 * es; }
-  }
-  std::memcpy(meta.data() + desc_b + woff_b, tasks.data(), (size_t)ntasks * sizeof(int4));
+  std::memcpy(meta.data() + desc_b, tasks.data(), (size_t)ntasks * sizeof(int4));
   if (!cap && st != ctx->stream && (sst = order_after(ctx, st, ctx->stream))) return sst;
   if ((sst = stage(ctx, ctx->grid_meta, meta.data(), meta.size(), st, cap))) return sst;
   const char* mdev = (const char*)ctx->grid_meta.dev.p;
   const InstDesc* desc_d = (const InstDesc*)mdev;
-  const int64_t* woff_d = (const int64_t*)(mdev + desc_b);
-  const int4* tasks_d = (const int4*)(mdev + desc_b + woff_b);
+  const int4* tasks_d = (const int4*)(mdev + desc_b);
   c128* rho = (c128*)ctx->fac.p;
   c128* x = rho + totN;
   c128* omega = x + totN;  // 2N per instance (2N-1 used)
@@ -648,16 +648,15 @@ lse_status lse_eval_grid_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* 
   c64* x32 = omega32 + 2 * totN;
   record(ctx, 1, st, true);
   cudaError_t e = launch_factor(ctx->cfg.precision == LSE_PREC_MIXED_DF, sfmin, Nmin, y_d, desc_d, B, Nmax, theta_d,
-                                gamma_d, beta_d,
-                                tables(ctx), ctx->ws.p, rho, x, omega, omega32, x32, delta, status,
+                                gamma_d, beta_d, tables(ctx), ctx->ws.p, rho, x, omega, omega32, x32, delta, status,
                                 !(ctx->cfg.flags & LSE_FLAG_NO_CLUSTER), st);
   record(ctx, 1, st, false);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "factor kernel launch");
   // schedule of the on-chip grid FFT: cached, or tuned now on this batch
   // (tuning waits for the device once; it is skipped while capturing)
   int variant = 1;
-  if (grid_on_chip(f32, Lmax)) {
-    const auto key = std::make_pair(f32 ? 1 : 0, Lmax);
+  if (n_small) {
+    const auto key = std::make_pair(f32 ? 1 : 0, Lmax_small);
     auto it = ctx->grid_variant.find(key);
     if (it != ctx->grid_variant.end()) {
       variant = it->second;
@@ -667,8 +666,8 @@ lse_status lse_eval_grid_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* 
       for (auto& x : ev) LSE_CUDA(ctx, cudaEventCreate(&x));
       cudaEventRecord(ev[0], st);
       for (int v = 0; v < nv; ++v) {
-        e = launch_grid(v, f32, desc_d, B, Lmax, rho, x, omega, x32, omega32, delta, tables(ctx), ctx->ws.p, woff_d,
-                        tasks_d, ntasks, q, dq, d2q, s, ds, d2s, st);
+        e = launch_grid(v, f32, desc_d, Lmax_small, 0, omega, x, omega32, x32, tables(ctx), ctx->ws.p, tasks_d,
+                        n_small, 0, q, dq, d2q, s, ds, d2s, st);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "grid kernel launch (autotune)");
         cudaEventRecord(ev[v + 1], st);
       }
@@ -685,8 +684,8 @@ lse_status lse_eval_grid_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* 
     }
   }
   record(ctx, 2, st, true);
-  e = launch_grid(variant, f32, desc_d, B, Lmax, rho, x, omega, x32, omega32, delta, tables(ctx), ctx->ws.p, woff_d,
-                  tasks_d, ntasks, q, dq, d2q, s, ds, d2s, st);
+  e = launch_grid(variant, f32, desc_d, Lmax_small, Lmax_large, omega, x, omega32, x32, tables(ctx), ctx->ws.p, tasks_d,
+                  n_small, n_large, q, dq, d2q, s, ds, d2s, st);
   record(ctx, 2, st, false);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "grid kernel launch");
   if (!cap && st != ctx->stream && (sst = order_after(ctx, ctx->stream, st))) return sst;

@@ -8,8 +8,9 @@
 //                 instance: first column of C, Levinson recursion
 //                 (Gohberg-Semencul generators rho, delta) and x = C^{-1} y
 //                 by FFT convolutions (Sec. III-A, III-B).
-//  grid_kernel    the length-L spectra of index-weighted generators and the
-//                 pointwise combine.  With c = (N-2)/2 and
+//  grid kernels   the length-L spectra (on chip, or in four steps for L too
+//                 large for one block) with the outputs written directly.
+//                 With c = (N-2)/2 and
 //                   Q_a = DFT_L((n-c)^a rho_n),  X_a = DFT_L(n^a x_n)
 //                 the grid quantities are (Appendix B weights, centred)
 //                   s   = (2/d) Re(Q1 Q0*)
@@ -17,6 +18,8 @@
 //                   s'' = (8 pi^2/d) [Re(Q2 Q1*) - Re(Q3 Q0*)]
 //                   q = X0,  q' = -j 2 pi X1,  q'' = -4 pi^2 X2
 //                 (d = delta_{N-1}; DFT_L(v)(l) = sum_n v_n e^{-j 2 pi n l / L}).
+#include <vector>
+
 #include "lse_device.cuh"
 #include "lse_df64.cuh"
 #include "lse_fft_smem.cuh"
@@ -248,76 +251,18 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
 }
 
 // ------------------------------------------------------------------ grid ---
-// One block per (instance, family): family 0 makes s, s', s'' from Q0..Q3,
-// family 1 makes q, q', q'' from X0..X2.  Spectra are built with the block
-// FFT in the workspace (L2-resident) and combined pointwise.
-template <class T>
-__global__ void __launch_bounds__(kFNT, 1)
-    grid_kernel(const InstDesc* inst, const c128* rho_all, const c128* x_all, const double* delta, Tables tab,
-                char* ws, const int64_t* ws_off, T* q, T* dq, T* d2q, T* s, T* ds, T* d2s) {
-  const int b = blockIdx.x >> 1, fam = blockIdx.x & 1;
-  const InstDesc d = inst[b];
-  const int N = d.N, L = d.L, log2L = ilog2((uint32_t)L);
-  const Twiddles<T> tw{(const cx<T>*)(sizeof(T) == 8 ? (const void*)tab.tw64 : (const void*)tab.tw32), tab.log2max};
-  cx<T>* buf = (cx<T>*)(ws + ws_off[b] + (size_t)fam * 5 * L * sizeof(cx<T>));
-  cx<T>* B[5];
-  for (int j = 0; j < 5; ++j) B[j] = buf + (size_t)j * L;
-  const int64_t g = d.g_off;
-  if (fam == 0) {
-    const c128* rho = rho_all + d.y_off;
-    const double cen = 0.5 * (double)(N - 2);
-    const double inv_d = 1.0 / delta[b];
-    for (int a = 0; a < 4; ++a) {
-      block_fft<kFNT, T>(
-          [=] __device__(int i) {
-            if (i >= N) return zero<T>();
-            const double w = (double)i - cen;
-            double p = 1.0;
-            for (int e = 0; e < a; ++e) p *= w;
-            return cvt<T>(p * rho[i]);
-          },
-          B[a], B[4], log2L, false, tw);
-    }
-    for (int l = threadIdx.x; l < L; l += kFNT) {
-      const cx<T> Q0 = B[0][l], Q1 = B[1][l], Q2 = B[2][l], Q3 = B[3][l];
-      const cx<T> q10 = Q1 * conj(Q0), q20 = Q2 * conj(Q0), q21 = Q2 * conj(Q1), q30 = Q3 * conj(Q0);
-      if (s) s[g + l] = (T)(2.0 * inv_d) * q10.re;
-      if (ds) ds[g + l] = (T)(4.0 * kPi * inv_d) * q20.im;
-      if (d2s) d2s[g + l] = (T)(8.0 * kPi * kPi * inv_d) * (q21.re - q30.re);
-    }
-  } else {
-    const c128* x = x_all + d.y_off;
-    for (int a = 0; a < 3; ++a) {
-      block_fft<kFNT, T>(
-          [=] __device__(int i) {
-            if (i >= N) return zero<T>();
-            double p = 1.0;
-            for (int e = 0; e < a; ++e) p *= (double)i;
-            return cvt<T>(p * x[i]);
-          },
-          B[a], B[4], log2L, false, tw);
-    }
-    cx<T>* Q = (cx<T>*)q;
-    cx<T>* DQ = (cx<T>*)dq;
-    cx<T>* D2Q = (cx<T>*)d2q;
-    for (int l = threadIdx.x; l < L; l += kFNT) {
-      if (Q) Q[g + l] = B[0][l];
-      if (DQ) DQ[g + l] = (T)(-kTwoPi) * mul_j(B[1][l]);
-      if (D2Q) D2Q[g + l] = (T)(-4.0 * kPi * kPi) * B[2][l];
-    }
-  }
-}
-
-
-// ------------------------------------------------------- grid (on chip) ---
-// Grid outputs as five independent length-L FFTs, each done by one block in
-// shared memory (lse_fft_smem.cuh):
+// Grid outputs as five independent length-L transforms per instance:
 //   job 0: Z = sum_i (1 - i/N) omega_s(i) e^{+j2pi i l/L} -> s = Re Z, s' = 2 pi N Im Z
 //          (s and s'/(2 pi N) are real transforms of Hermitian sequences and
 //          share one complex FFT; the 1/(2 pi N) keeps both parts the same size)
 //   job 1: s'' = Re sum_i (-4 pi^2 i^2) omega_s(i) e^{+j2pi i l/L}
 //   jobs 2-4: q^(a) = sum_n (-j 2 pi n)^a x_n e^{-j2pi n l/L}, a = 0, 1, 2
 // (Sec. III-D: the grid vectors are FFTs; omega_s from the factor kernel.)
+// A task is (instance, job, partner, aux): a paired s'' job also transforms a
+// second instance of the same N and L in the imaginary part (both inputs
+// Hermitian, both outputs real).  GridJob gives a task's input sequence and
+// takes its outputs; the on-chip kernel (one block per task, L on chip) and
+// the four-step kernels (L too large for one block) share it.
 template <class T>
 struct GridPtrs {
   T *q, *dq, *d2q, *s, *ds, *d2s;
@@ -326,40 +271,19 @@ struct GridPtrs {
 template <class T>
 __host__ __device__ constexpr int grid_mmax() { return sizeof(T) == 4 ? 16384 : 8192; }
 
-template <class T, int NT, bool R16>
-__global__ void __launch_bounds__(NT)
-    grid_fft_kernel(const InstDesc* inst, const cx<T>* omega_all, const cx<T>* x_all, Tables tab, GridPtrs<T> out,
-                    const int4* tasks) {
-  extern __shared__ __align__(16) char gsm[];
-  // task: x = instance, y = job, z = partner instance of a paired s'' job (or -1)
-  const int4 task = tasks[blockIdx.x];
-  const int b = task.x, job = task.y, b2 = task.z;
-  const InstDesc d = inst[b];
-  const int N = d.N, L = d.L, log2L = ilog2((uint32_t)L);
-  const int64_t g = d.g_off;
-  cx<T>* sm = (cx<T>*)gsm;
-  cx<T>* tlo = sm + L + (L >> 4);
-  cx<T>* thi = tlo + (1 << ((log2L + 1) >> 1));
-  const cx<T>* gtw = (const cx<T>*)(sizeof(T) == 8 ? (const void*)tab.tw64 : (const void*)tab.tw32);
-  const SmemTwiddles<T> tw = make_smem_twiddles<NT, T>(tlo, thi, log2L, gtw, tab.log2max);
-  constexpr int MMAX = grid_mmax<T>();
-  // one FFT instantiation for every job (the job only changes the input
-  // functor, the direction and the epilogue) keeps the kernel's code small
-  const cx<T>* om = omega_all + 2 * d.y_off + (N - 1);  // om[i], |i| < N
-  // a paired s'' job also transforms a second instance of the same N and L in
-  // the imaginary part (both inputs are Hermitian, both outputs real)
-  const cx<T>* om2 = b2 >= 0 ? omega_all + 2 * inst[b2].y_off + (N - 1) : om;
-  const int64_t g2 = b2 >= 0 ? inst[b2].g_off : 0;
-  const cx<T>* x = x_all + d.y_off;
-  // scalars in the element type: the FP64 pipe is slow enough that a per-
-  // thread FP64 division showed up in the profile
-  const T invN = (T)1 / (T)N;
-  const T fpp = (T)(-4.0 * kPi * kPi);
-  const T tp = (T)kTwoPi;
-  auto gen = [=] __device__(int l) {
+template <class T>
+struct GridJob {
+  int N, L, job;
+  bool pair;
+  int64_t g, g2;
+  const cx<T> *om, *om2, *x;
+  T invN, fpp, tp, f;
+  T *o0, *o1;
+  // input sequence at l (the lag i = l mod L for the s jobs)
+  __device__ __forceinline__ cx<T> in(int l) const {
     cx<T> v = zero<T>();
     if (job <= 1) {
-      const int i = l < N ? l : l - L;  // lag stored at l = i mod L
+      const int i = l < N ? l : l - L;
       if (i > -N && i < N) {
         const cx<T> o = om[i];
         const T fi = (T)i;
@@ -367,7 +291,7 @@ __global__ void __launch_bounds__(NT)
           v = ((T)1 - fi * invN) * o;
         } else {
           v = (fpp * fi * fi) * o;
-          if (b2 >= 0) v = v + mul_j((fpp * fi * fi) * om2[i]);
+          if (pair) v = v + mul_j((fpp * fi * fi) * om2[i]);
         }
       }
     } else if (l < N) {
@@ -377,21 +301,205 @@ __global__ void __launch_bounds__(NT)
       if (job == 4) v = (-w * w) * v;
     }
     return v;
-  };
-  T* o0 = job == 0 ? out.s : job == 1 ? out.d2s : job == 2 ? out.q : job == 3 ? out.dq : out.d2q;
-  T* o1 = job == 0 ? out.ds : (b2 >= 0 ? out.d2s : nullptr);
-  const T f = job == 0 ? tp * (T)N : (T)1;
-  const int64_t go = job == 0 ? g : g2;
-  auto epi = [=] __device__(int l, cx<T> z) {
+  }
+  __device__ __forceinline__ void out(int l, cx<T> z) const {
     if (job >= 2) {
       ((cx<T>*)o0)[g + l] = z;
     } else {
       if (o0) o0[g + l] = z.re;
-      if (o1) o1[go + l] = f * z.im;
+      if (o1) o1[(job == 0 ? g : g2) + l] = f * z.im;
     }
-  };
+  }
+  __device__ __forceinline__ bool inverse() const { return job <= 1; }
+};
+
+template <class T>
+__device__ __forceinline__ GridJob<T> make_grid_job(const InstDesc* inst, int4 task, const cx<T>* omega_all,
+                                                   const cx<T>* x_all, const GridPtrs<T>& out) {
+  GridJob<T> J;
+  const int b = task.x, b2 = task.z;
+  const InstDesc d = inst[b];
+  J.N = d.N;
+  J.L = d.L;
+  J.job = task.y;
+  J.pair = b2 >= 0;
+  J.g = d.g_off;
+  J.g2 = b2 >= 0 ? inst[b2].g_off : 0;
+  J.om = omega_all + 2 * d.y_off + (d.N - 1);  // om[i], |i| < N
+  J.om2 = b2 >= 0 ? omega_all + 2 * inst[b2].y_off + (d.N - 1) : J.om;
+  J.x = x_all + d.y_off;
+  // scalars in the element type: the FP64 pipe is slow enough that a per-
+  // thread FP64 division showed up in the profile
+  J.invN = (T)1 / (T)d.N;
+  J.fpp = (T)(-4.0 * kPi * kPi);
+  J.tp = (T)kTwoPi;
+  const int job = J.job;
+  J.o0 = job == 0 ? out.s : job == 1 ? out.d2s : job == 2 ? out.q : job == 3 ? out.dq : out.d2q;
+  J.o1 = job == 0 ? out.ds : (J.pair ? out.d2s : nullptr);
+  J.f = job == 0 ? J.tp * (T)d.N : (T)1;
+  return J;
+}
+
+// ------------------------------------------------------- grid (on chip) ---
+// One block per task, the whole length-L FFT in shared memory
+// (lse_fft_smem.cuh): the first pass reads the input through the task's
+// generator and the last pass writes the outputs straight to global memory.
+template <class T, int NT, bool R16>
+__global__ void __launch_bounds__(NT)
+    grid_fft_kernel(const InstDesc* inst, const cx<T>* omega_all, const cx<T>* x_all, Tables tab, GridPtrs<T> out,
+                    const int4* tasks) {
+  extern __shared__ __align__(16) char gsm[];
+  const GridJob<T> J = make_grid_job<T>(inst, tasks[blockIdx.x], omega_all, x_all, out);
+  const int log2L = ilog2((uint32_t)J.L);
+  cx<T>* sm = (cx<T>*)gsm;
+  cx<T>* tlo = sm + J.L + (J.L >> 4);
+  cx<T>* thi = tlo + (1 << ((log2L + 1) >> 1));
+  const cx<T>* gtw = (const cx<T>*)(sizeof(T) == 8 ? (const void*)tab.tw64 : (const void*)tab.tw32);
+  const SmemTwiddles<T> tw = make_smem_twiddles<NT, T>(tlo, thi, log2L, gtw, tab.log2max);
+  constexpr int MMAX = grid_mmax<T>();
   __syncthreads();  // twiddle tables
-  smem_fft_run<NT, MMAX, R16, T>(gen, sm, log2L, job <= 1, tw, epi);
+  smem_fft_run<NT, MMAX, R16, T>([&] __device__(int l) { return J.in(l); }, sm, log2L, J.inverse(), tw,
+                                 [&] __device__(int l, cx<T> z) { J.out(l, z); });
+}
+
+// ----------------------------------------------------- grid (four-step) ---
+// L too large for one block: L = L1 L2 (L1 = 2^ceil(p/2), L2 = 2^floor(p/2),
+// L = 2^p), and with m = L2 n1 + n2, k = k1 + L1 k2 the transform is
+//   Y[k1][n2] = W_L^{n2 k1} sum_{n1} x[L2 n1 + n2] W_{L1}^{n1 k1}   (columns)
+//   X[k1 + L1 k2] = sum_{n2} Y[k1][n2] W_{L2}^{n2 k2}               (rows)
+// (W = e^{-+j 2 pi / .}).  Y (one length-L buffer per task) lives in the
+// workspace and stays in L2.  Each block transforms a few columns (or rows)
+// at once in shared memory; loads and stores run over consecutive columns
+// (rows) so that they coalesce.  Tasks of several sizes share a launch: a
+// block past its task's extent returns.
+constexpr int kG4Threads = 256;
+constexpr int kG4SmemBytes = 64 * 1024;  // two ping-pong buffers
+
+// sequences of length len a block transforms at once (count of them in all):
+// up to 8, as shared memory allows, never more than there are
+template <class T>
+__host__ __device__ inline int g4_group(int len, int count) {
+  int g = kG4SmemBytes / (2 * len * (int)sizeof(cx<T>));
+  if (g > 8) g = 8;
+  return g < count ? g : count;
+}
+
+// nb sequences of length 2^lg at a + f 2^lg, radix-4/2 Stockham between a and
+// b; returns the buffer holding the result.
+template <class T, int NT>
+__device__ cx<T>* smem_batch_fft(cx<T>* a, cx<T>* b, int nb, int lg, bool inverse, const cx<T>* tw, int log2max) {
+  const int n = 1 << lg;
+  int len = n, s = 1, log2s = 0;
+  cx<T>* in = a;
+  cx<T>* out = b;
+  while (len >= 4) {
+    const int n4 = len >> 2;
+    for (int t = threadIdx.x; t < (nb << (lg - 2)); t += NT) {
+      const int f = t >> (lg - 2), tt = t & ((n >> 2) - 1);
+      const int p = tt >> log2s, q = tt & (s - 1);
+      const cx<T>* i0 = in + (size_t)f * n;
+      cx<T>* o0 = out + (size_t)f * n;
+      const cx<T> x0 = i0[q + s * p], x1 = i0[q + s * (p + n4)], x2 = i0[q + s * (p + 2 * n4)], x3 = i0[q + s * (p + 3 * n4)];
+      const cx<T> apc = x0 + x2, amc = x0 - x2, bpd = x1 + x3, jbmd = mul_j(x1 - x3);
+      const cx<T> y1 = inverse ? amc + jbmd : amc - jbmd;
+      const cx<T> y3 = inverse ? amc - jbmd : amc + jbmd;
+      const cx<T> y2 = apc - bpd;
+      const int sh = log2max - lg;
+      cx<T> w1 = tw[(size_t)(p * s) << sh], w2 = tw[(size_t)(2 * p * s) << sh], w3 = tw[(size_t)(3 * p * s) << sh];
+      if (inverse) { w1 = conj(w1); w2 = conj(w2); w3 = conj(w3); }
+      o0[q + s * (4 * p + 0)] = apc + bpd;
+      o0[q + s * (4 * p + 1)] = w1 * y1;
+      o0[q + s * (4 * p + 2)] = w2 * y2;
+      o0[q + s * (4 * p + 3)] = w3 * y3;
+    }
+    __syncthreads();
+    cx<T>* t2 = in; in = out; out = t2;
+    len >>= 2; s <<= 2; log2s += 2;
+  }
+  if (len == 2) {
+    for (int t = threadIdx.x; t < (nb << (lg - 1)); t += NT) {
+      const int f = t >> (lg - 1), q = t & ((n >> 1) - 1);
+      const cx<T>* i0 = in + (size_t)f * n;
+      cx<T>* o0 = out + (size_t)f * n;
+      const cx<T> x0 = i0[q], x1 = i0[q + s];
+      o0[q] = x0 + x1;
+      o0[q + s] = x0 - x1;
+    }
+    __syncthreads();
+    cx<T>* t2 = in; in = out; out = t2;
+  }
+  return in;
+}
+
+__host__ __device__ inline void g4_split(int L, int& p1, int& p2) {
+  const int p = ilog2((uint32_t)L);
+  p1 = (p + 1) >> 1;
+  p2 = p - p1;
+}
+
+// columns: block (cb, task) transforms columns n2 in [cb G, cb G + G)
+template <class T>
+__global__ void __launch_bounds__(kG4Threads)
+    grid4_cols_kernel(const InstDesc* inst, const cx<T>* omega_all, const cx<T>* x_all, Tables tab, GridPtrs<T> out,
+                      const int4* tasks, cx<T>* ws) {
+  extern __shared__ __align__(16) char gsm[];
+  const int4 task = tasks[blockIdx.y];
+  const GridJob<T> J = make_grid_job<T>(inst, task, omega_all, x_all, out);
+  int p1, p2;
+  g4_split(J.L, p1, p2);
+  const int L1 = 1 << p1, L2 = 1 << p2;
+  const int G = g4_group<T>(L1, L2);
+  const int c0 = blockIdx.x * G;
+  if (c0 >= L2) return;
+  cx<T>* a = (cx<T>*)gsm;
+  cx<T>* b = a + (size_t)G * L1;
+  for (int e = threadIdx.x; e < G * L1; e += kG4Threads) {
+    const int n1 = e / G, f = e - n1 * G;
+    a[(size_t)f * L1 + n1] = J.in(L2 * n1 + c0 + f);
+  }
+  __syncthreads();
+  const cx<T>* tw = (const cx<T>*)(sizeof(T) == 8 ? (const void*)tab.tw64 : (const void*)tab.tw32);
+  const bool inv = J.inverse();
+  const cx<T>* r = smem_batch_fft<T, kG4Threads>(a, b, G, p1, inv, tw, tab.log2max);
+  cx<T>* Y = ws + (int64_t)task.w * 1024;
+  const int p = p1 + p2;
+  const int sh = tab.log2max - p;
+  const int msk = J.L - 1;
+  for (int e = threadIdx.x; e < G * L1; e += kG4Threads) {
+    const int k1 = e / G, f = e - k1 * G;
+    const int n2 = c0 + f;
+    cx<T> w = tw[(size_t)((n2 * k1) & msk) << sh];
+    if (inv) w = conj(w);
+    Y[(size_t)k1 * L2 + n2] = w * r[(size_t)f * L1 + k1];
+  }
+}
+
+// rows: block (rb, task) transforms rows k1 in [rb G, rb G + G) and writes
+// the outputs X[k1 + L1 k2]
+template <class T>
+__global__ void __launch_bounds__(kG4Threads)
+    grid4_rows_kernel(const InstDesc* inst, const cx<T>* omega_all, const cx<T>* x_all, Tables tab, GridPtrs<T> out,
+                      const int4* tasks, const cx<T>* ws) {
+  extern __shared__ __align__(16) char gsm[];
+  const int4 task = tasks[blockIdx.y];
+  const GridJob<T> J = make_grid_job<T>(inst, task, omega_all, x_all, out);
+  int p1, p2;
+  g4_split(J.L, p1, p2);
+  const int L1 = 1 << p1, L2 = 1 << p2;
+  const int G = g4_group<T>(L2, L1);
+  const int r0 = blockIdx.x * G;
+  if (r0 >= L1) return;
+  cx<T>* a = (cx<T>*)gsm;
+  cx<T>* b = a + (size_t)G * L2;
+  const cx<T>* Y = ws + (int64_t)task.w * 1024;
+  for (int e = threadIdx.x; e < G * L2; e += kG4Threads) a[e] = Y[(size_t)r0 * L2 + e];
+  __syncthreads();
+  const cx<T>* tw = (const cx<T>*)(sizeof(T) == 8 ? (const void*)tab.tw64 : (const void*)tab.tw32);
+  const cx<T>* r = smem_batch_fft<T, kG4Threads>(a, b, G, p2, J.inverse(), tw, tab.log2max);
+  for (int e = threadIdx.x; e < G * L2; e += kG4Threads) {
+    const int k2 = e / G, f = e - k2 * G;
+    J.out(r0 + f + L1 * k2, r[(size_t)f * L2 + k2]);
+  }
 }
 
 }  // namespace
@@ -463,15 +571,13 @@ cudaError_t launch_factor(bool df, int sf_min_n, int Nmin, const float* y, const
                                      omega_out, omega32_out, x32_out, delta_out, status, false, stream);
 }
 
-size_t grid_workspace_bytes(int B, int64_t total_L, bool f32) {
-  (void)B;
-  return (size_t)total_L * 2 * 5 * (f32 ? sizeof(c64) : sizeof(c128));
-}
+size_t grid_workspace_bytes(size_t ws_elems, bool f32) { return ws_elems * (f32 ? sizeof(c64) : sizeof(c128)); }
 
-// Schedules of the on-chip grid FFT: (threads per block, radix-16 passes).
-// The autotuner in lse_api.cu times them on the live batch and keeps the
-// fastest per (element type, grid size).
-static const GridVariant kGridVariants[] = {{256, true}, {512, true}, {1024, true}, {512, false}};
+// Schedules of the grid FFT for grids that fit on chip: the on-chip kernel
+// with (threads per block, radix-16 passes), or (threads 0) the four-step
+// kernels.  The autotuner in lse_api.cu times them on the live batch and
+// keeps the fastest per (element type, grid size).
+static const GridVariant kGridVariants[] = {{256, true}, {512, true}, {1024, true}, {512, false}, {0, false}};
 int grid_variant_count() { return (int)(sizeof(kGridVariants) / sizeof(kGridVariants[0])); }
 GridVariant grid_variant(int i) { return kGridVariants[i]; }
 
@@ -500,48 +606,95 @@ static cudaError_t launch_grid_fft(int variant, const InstDesc* inst, const int4
   }
 }
 
-int grid_tasks(const InstDesc* inst, int B, bool q, bool dq, bool d2q, bool s, bool ds, bool d2s, int4* out) {
-  int n = 0;
+// Tasks of a batch: one per (instance, output family); the s'' jobs of
+// consecutive instances of equal N and L share one.  The tasks the on-chip
+// kernel can take come first (n_small of them), then those whose L is too
+// large for it.  Every task carries the offset of its four-step intermediate
+// buffer (in units of 1024 elements) in .w (any task may run in four steps);
+// *ws_elems receives the intermediate buffers' total size.
+int grid_tasks(const InstDesc* inst, int B, bool f32, bool q, bool dq, bool d2q, bool s, bool ds, bool d2s, int4* out,
+               int* n_small, size_t* ws_elems) {
+  std::vector<int4> all;
   int pend = -1;  // an instance whose s'' job waits for a partner of the same N and L
   for (int b = 0; b < B; ++b) {
-    if (s || ds) out[n++] = make_int4(b, 0, -1, 0);
-    if (q) out[n++] = make_int4(b, 2, -1, 0);
-    if (dq) out[n++] = make_int4(b, 3, -1, 0);
-    if (d2q) out[n++] = make_int4(b, 4, -1, 0);
+    if (s || ds) all.push_back(make_int4(b, 0, -1, 0));
+    if (q) all.push_back(make_int4(b, 2, -1, 0));
+    if (dq) all.push_back(make_int4(b, 3, -1, 0));
+    if (d2q) all.push_back(make_int4(b, 4, -1, 0));
     if (d2s) {
       if (pend >= 0 && inst[pend].N == inst[b].N && inst[pend].L == inst[b].L) {
-        out[n++] = make_int4(pend, 1, b, 0);
+        all.push_back(make_int4(pend, 1, b, 0));
         pend = -1;
       } else {
-        if (pend >= 0) out[n++] = make_int4(pend, 1, -1, 0);
+        if (pend >= 0) all.push_back(make_int4(pend, 1, -1, 0));
         pend = b;
       }
     }
   }
-  if (pend >= 0) out[n++] = make_int4(pend, 1, -1, 0);
+  if (pend >= 0) all.push_back(make_int4(pend, 1, -1, 0));
+  const int lim = f32 ? grid_mmax<float>() : grid_mmax<double>();
+  int n = 0, ns = 0;
+  size_t off = 0;
+  for (int pass = 0; pass < 2; ++pass)
+    for (const int4& t : all) {
+      const int L = inst[t.x].L;
+      if ((L <= lim) != (pass == 0)) continue;
+      out[n++] = make_int4(t.x, t.y, t.z, (int)(off / 1024));
+      off += (size_t)(L < 1024 ? 1024 : L);
+      ns += pass == 0;
+    }
+  *n_small = ns;
+  *ws_elems = off;
   return n;
 }
 
-bool grid_on_chip(bool f32, int Lmax) { return Lmax <= (f32 ? grid_mmax<float>() : grid_mmax<double>()); }
+bool grid_on_chip(bool f32, int L) { return L <= (f32 ? grid_mmax<float>() : grid_mmax<double>()); }
 
-cudaError_t launch_grid(int variant, bool f32, const InstDesc* inst, int B, int Lmax, const c128* rho, const c128* x,
-                        const c128* omega, const c64* x32, const c64* omega32, const double* delta, const Tables& tab,
-                        void* ws, const int64_t* ws_off, const int4* tasks, int ntasks, void* q, void* dq, void* d2q,
-                        void* s, void* ds, void* d2s, cudaStream_t stream) {
-  if (grid_on_chip(f32, Lmax))
-    return f32 ? launch_grid_fft<float>(variant, inst, tasks, ntasks, omega32, x32, tab, Lmax, q, dq, d2q, s, ds, d2s,
-                                        stream)
-               : launch_grid_fft<double>(variant, inst, tasks, ntasks, omega, x, tab, Lmax, q, dq, d2q, s, ds, d2s,
-                                         stream);
-  // instance b's buffers start ws_off[b] bytes into ws
-  char* base = (char*)ws;
-  if (f32)
-    grid_kernel<float><<<2 * B, kFNT, 0, stream>>>(inst, rho, x, delta, tab, base, ws_off, (float*)q, (float*)dq,
-                                                   (float*)d2q, (float*)s, (float*)ds, (float*)d2s);
-  else
-    grid_kernel<double><<<2 * B, kFNT, 0, stream>>>(inst, rho, x, delta, tab, base, ws_off, (double*)q, (double*)dq,
-                                                    (double*)d2q, (double*)s, (double*)ds, (double*)d2s);
+template <class T>
+static cudaError_t launch_grid4(const InstDesc* inst, const int4* tasks, int n, int Lmax, const cx<T>* omega,
+                                const cx<T>* x, const Tables& tab, void* ws, const GridPtrs<T>& o,
+                                cudaStream_t stream) {
+  if (!n) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(grid4_cols_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kG4SmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(grid4_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kG4SmemBytes);
+  if (e != cudaSuccess) return e;
+  int p1, p2;
+  g4_split(Lmax, p1, p2);
+  // the largest L needs the most blocks per task (smaller L need no more)
+  const int gx_cols = (1 << p2) / g4_group<T>(1 << p1, 1 << p2);
+  const int gx_rows = (1 << p1) / g4_group<T>(1 << p2, 1 << p1);
+  grid4_cols_kernel<T><<<dim3(gx_cols, n), kG4Threads, kG4SmemBytes, stream>>>(inst, omega, x, tab, o, tasks,
+                                                                             (cx<T>*)ws);
+  grid4_rows_kernel<T><<<dim3(gx_rows, n), kG4Threads, kG4SmemBytes, stream>>>(inst, omega, x, tab, o, tasks,
+                                                                             (const cx<T>*)ws);
   return cudaGetLastError();
+}
+
+cudaError_t launch_grid(int variant, bool f32, const InstDesc* inst, int Lmax_small, int Lmax_large, const c128* omega,
+                        const c128* x, const c64* omega32, const c64* x32, const Tables& tab, void* ws,
+                        const int4* tasks, int n_small, int n_large, void* q, void* dq, void* d2q, void* s, void* ds,
+                        void* d2s, cudaStream_t stream) {
+  cudaError_t e = cudaSuccess;
+  if (n_small && kGridVariants[variant].threads == 0) {  // everything in four steps
+    n_large += n_small;
+    Lmax_large = Lmax_large > Lmax_small ? Lmax_large : Lmax_small;
+    n_small = 0;
+  }
+  if (n_small)
+    e = f32 ? launch_grid_fft<float>(variant, inst, tasks, n_small, omega32, x32, tab, Lmax_small, q, dq, d2q, s, ds,
+                                     d2s, stream)
+            : launch_grid_fft<double>(variant, inst, tasks, n_small, omega, x, tab, Lmax_small, q, dq, d2q, s, ds,
+                                      d2s, stream);
+  if (e != cudaSuccess || !n_large) return e;
+  if (f32)
+    return launch_grid4<float>(inst, tasks + n_small, n_large, Lmax_large, omega32, x32, tab, ws,
+                               GridPtrs<float>{(float*)q, (float*)dq, (float*)d2q, (float*)s, (float*)ds, (float*)d2s},
+                               stream);
+  return launch_grid4<double>(inst, tasks + n_small, n_large, Lmax_large, omega, x, tab, ws,
+                              GridPtrs<double>{(double*)q, (double*)dq, (double*)d2q, (double*)s, (double*)ds,
+                                               (double*)d2s},
+                              stream);
 }
 
 }  // namespace lse

@@ -86,20 +86,24 @@ struct GridVariant {
 int grid_variant_count();
 GridVariant grid_variant(int i);
 
-// rho, x: [sum N]; omega: instance b's 2N-1 diagonal sums at 2*y_off.
-// variant: index of the on-chip schedule (ignored for grids too large for it).
-// ws, ws_off (device, B entries): workspace of the global-memory grid kernel,
-// instance b's buffers ws_off[b] bytes into ws (unused by the on-chip kernel).
-cudaError_t launch_grid(int variant, bool f32, const InstDesc* inst, int B, int Lmax, const c128* rho, const c128* x,
-                        const c128* omega, const c64* x32, const c64* omega32, const double* delta, const Tables& tab,
-                        void* ws, const int64_t* ws_off, const int4* tasks, int ntasks, void* q, void* dq, void* d2q,
-                        void* s, void* ds, void* d2s, cudaStream_t stream);
-// The on-chip grid kernel's task list for a batch (host): one block per
-// (instance, output family); the s'' transforms of consecutive instances of
-// equal N and L share one block.  `out` needs 5 B entries; returns the count.
-int grid_tasks(const InstDesc* inst, int B, bool q, bool dq, bool d2q, bool s, bool ds, bool d2s, int4* out);
-// true when every grid of the batch fits the on-chip FFT kernel (no workspace needed)
-bool grid_on_chip(bool f32, int Lmax);
-size_t grid_workspace_bytes(int B, int64_t total_L, bool f32);
+// Grid outputs of a batch from the factor kernel's omega_s and x (complex128,
+// and their complex64 copies for the FP32 outputs).  tasks: the n_small
+// on-chip tasks, then the n_large four-step tasks (grid_tasks); ws: the
+// four-step intermediate buffers (grid_workspace_bytes); variant: the on-chip
+// schedule; Lmax_small / Lmax_large: the largest L of each group.
+cudaError_t launch_grid(int variant, bool f32, const InstDesc* inst, int Lmax_small, int Lmax_large, const c128* omega,
+                        const c128* x, const c64* omega32, const c64* x32, const Tables& tab, void* ws,
+                        const int4* tasks, int n_small, int n_large, void* q, void* dq, void* d2q, void* s, void* ds,
+                        void* d2s, cudaStream_t stream);
+// The grid tasks of a batch (host): one per (instance, output family), the
+// s'' transforms of consecutive instances of equal N and L paired; the tasks
+// with L small enough for the on-chip kernel first (*n_small), then the others
+// with their intermediate offsets; *ws_elems the intermediates' total length.
+// `out` needs 5 B entries; returns the count.
+int grid_tasks(const InstDesc* inst, int B, bool f32, bool q, bool dq, bool d2q, bool s, bool ds, bool d2s, int4* out,
+               int* n_small, size_t* ws_elems);
+// whether a grid of size L fits the on-chip FFT kernel
+bool grid_on_chip(bool f32, int L);
+size_t grid_workspace_bytes(size_t ws_elems, bool f32);
 
 }  // namespace lse

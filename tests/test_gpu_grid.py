@@ -164,3 +164,41 @@ def test_grid_batch_captured_in_cuda_graph(ctxs, which):
         torch.cuda.synchronize()
         for f in FIELDS:
             assert torch.equal(graphed[f], direct[f]), f
+
+
+@pytest.mark.parametrize("which", [0, 2])
+def test_grid_batch_mixing_on_chip_and_four_step_sizes(ctxs, which):
+    """One batched launch whose grids are partly small enough for the on-chip
+    FFT kernel and partly larger (the four-step kernels: L above 16384 points
+    in FP32, 8192 in FP64), with two equal large instances whose s'' shares a
+    transform; every instance against the dense oracle at sampled points."""
+    import torch
+    from paper_1705_06073_gb300 import lse
+    f64 = which == 0
+    specs = [(200, 4, 512), (1000, 8, 32768), (1000, 6, 32768), (300, 5, 65536), (2000, 12, 16384), (64, 2, 128)]
+    ys, ths, gas, bes = [], [], [], []
+    for i, (N, K, L) in enumerate(specs):
+        y, th, ga, be = state(N, K, 3300 + i)
+        ys.append(y); ths.append(th); gas.append(ga); bes.append(be)
+    yo = np.concatenate([[0], np.cumsum([len(y) for y in ys])])
+    ko = np.concatenate([[0], np.cumsum([len(t) for t in ths])])
+    Ls = np.array([s[2] for s in specs], np.int32)
+    dev = torch.device("cuda:0")
+    y_d = torch.from_numpy(np.concatenate(ys)).to(dev)
+    th_d = torch.from_numpy(np.concatenate(ths + [np.zeros(1)])).to(dev)
+    ga_d = torch.from_numpy(np.concatenate(gas + [np.zeros(1)])).to(dev)
+    be_d = torch.tensor(bes, dtype=torch.float64, device=dev)
+    G = int(Ls.sum())
+    ct, rt = (torch.complex128, torch.float64) if f64 else (torch.complex64, torch.float32)
+    outs = {f: torch.zeros(G, dtype=ct if f in ("q", "dq", "d2q") else rt, device=dev) for f in FIELDS}
+    lse.lse_eval_grid_batch_d(ctxs[which], y_d, yo, th_d, ga_d, ko, be_d, Ls, outs, f64)
+    torch.cuda.synchronize()
+    g0 = 0
+    r = np.random.default_rng(77)
+    for i, (N, K, L) in enumerate(specs):
+        pts = np.unique(np.concatenate([r.integers(0, L, 150), np.mod(np.round(ths[i] * L).astype(int), L)]))
+        ref = dn.DenseEval(ys[i], ths[i], gas[i], bes[i]).grid(L, derivatives=True, points=pts / L)
+        got = {f: outs[f][g0:g0 + L].cpu().numpy()[pts] for f in FIELDS}
+        err = grid_errors(got, ref, N)
+        assert max(err.values()) < (1e-8 if f64 else 1e-4), (i, err)
+        g0 += L
