@@ -150,15 +150,29 @@ def approximate_activation_select(dl, q, s, gbar, zeta: float, theta_active, N: 
     gamma-bar of that evaluation (a scalar, or one value per grid point when no
     component is active, R4); theta_active: the frequencies active before the
     pass; K_room: how many more components the model may hold (K_max - K).
+    A candidate is taken when its eq. (activate_gamma) value is > 0 and eq.
+    (activate_derived) holds (no tau); the rest of the rules are those of
+    ``select_candidates``.  Returns [(l, gamma_hat)] in the order taken."""
+    s = np.asarray(s, dtype=np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ghat = dn.activate_gamma(q, s)
+        gb = np.broadcast_to(np.asarray(gbar, dtype=np.float64), s.shape)
+        passes = dn.activation_test(q, s, gb, zeta, 0.0)
+    return select_candidates(dl, ghat, passes, theta_active, N, L, K_room)
+
+
+def select_candidates(dl, ghat, passes, theta_active, N: int, L: int, K_room: int):
+    """Sec. II-E (reading R6) given, per grid point, the variance a component
+    would get there (ghat) and whether the activation test holds (passes).
+
     Candidates are the cyclic local minima Delta L(l) < Delta L(l-1),
     Delta L(l) <= Delta L(l+1) (a plateau keeps its first point).  With
     Delta L_min the smallest candidate value, nothing happens unless
     Delta L_min < 0; otherwise the candidates are visited in ascending
     Delta L (ties by index) while Delta L <= Delta L_min / 5, and a candidate
-    is taken when its eq. (activate_gamma) value is > 0, eq. (activate_derived)
-    holds (no tau) and it lies at wrap distance >= 0.05/N from every active
-    frequency, those taken earlier in the same pass included.
-    Returns [(l, gamma_hat)] in the order taken."""
+    is taken when ghat > 0, the test holds and it lies at wrap distance
+    >= 0.05/N from every active frequency, those taken earlier in the same
+    pass included.  Returns [(l, gamma_hat)] in the order taken."""
     dl = np.asarray(dl, dtype=np.float64)
     left = np.roll(dl, 1)
     right = np.roll(dl, -1)
@@ -176,16 +190,15 @@ def approximate_activation_select(dl, q, s, gbar, zeta: float, theta_active, N: 
             break
         if len(taken) >= K_room:
             break
-        ghat = float(dn.activate_gamma(q[l], s[l]))
-        if not ghat > 0.0:
+        gh = float(ghat[l])
+        if not gh > 0.0:
             continue
-        gb = float(gbar if np.ndim(gbar) == 0 else gbar[l])
-        if not dn.activation_test(q[l], s[l], gb, zeta, 0.0):
+        if not bool(passes[l]):
             continue
         th = l / L
         if active and np.min(_wrap(th, np.array(active))) < 0.05 / N:
             continue
-        taken.append((int(l), ghat))
+        taken.append((int(l), gh))
         active.append(th)
     return taken
 

@@ -134,6 +134,41 @@ def make_instance(N: int, K: int, snr_db: float, seed: int, *, law: str = "cn",
     return Instance(y=y, theta=theta, alpha=alpha, beta=beta, snr_db=snr_db, seed=seed)
 
 
+@dataclasses.dataclass
+class MMVInstance:
+    Y: np.ndarray  # complex64 [G, N]: snapshot g is Y[g] (snapshot-major, as the C ABI)
+    theta: np.ndarray  # true frequencies, shared by the snapshots
+    alpha: np.ndarray  # true coefficients [G, K]
+    beta: float  # true noise variance
+    snr_db: float
+    seed: int
+
+    @property
+    def N(self) -> int:
+        return int(self.Y.shape[1])
+
+    @property
+    def G(self) -> int:
+        return int(self.Y.shape[0])
+
+
+def make_mmv_instance(N: int, K: int, G: int, snr_db: float, seed: int, *, law: str = "cn",
+                      min_sep: float | None = None) -> MMVInstance:
+    """y^(g) = sum_k alpha_k^(g) e^{j 2 pi theta_k n} + w^(g), g = 1..G (the
+    multiple-measurement-vector model of Sec. V): the frequencies are shared,
+    each snapshot draws its own coefficients and noise.  The noise variance
+    is set from the mean per-snapshot SNR, sum_g ||Psi alpha^(g)||^2 / (G N beta)."""
+    st = Stream(seed)
+    sep = (2.0 / N) if min_sep is None else min_sep
+    theta = draw_frequencies(st, K, sep)
+    alpha = np.stack([draw_amplitudes(st, K, law) for _ in range(G)])
+    H = np.stack([sum_of_sinusoids(N, theta, alpha[g]) for g in range(G)])
+    beta = float(np.sum(np.abs(H) ** 2) / (G * N * 10.0 ** (snr_db / 10.0))) if K else 1.0
+    W = np.stack([math.sqrt(beta) * st.cnormal(N) for _ in range(G)])
+    return MMVInstance(Y=(H + W).astype(np.complex64), theta=theta, alpha=alpha, beta=beta,
+                       snr_db=snr_db, seed=seed)
+
+
 def default_grid_size(N: int) -> int:
     """L = 8N rounded to the nearest power of two (Sec. II-D footnote)."""
     return 1 << int(round(math.log2(8 * N)))
@@ -204,3 +239,14 @@ def make_request(spec):
 def paper_accuracy_n128(trial: int, seed0: int = 601):
     """N=128, K=10, 20 dB, the paper's amplitude law (Sec. VI-A, Fig. 2)."""
     return make_instance(128, 10, 20.0, seed0 + trial, law="paper"), 1024
+
+
+def mmv_batch(seed0: int = 701, B: int = 64, N: int = 1024, G: int = 8, K: int = 32):
+    """B multiple-measurement-vector instances (Sec. V): N = 1024 samples, G = 8
+    snapshots sharing K = 32 frequencies (separation 2/N, alpha ~ CN(0,1) per
+    snapshot), SNR uniform on [0, 20] dB per instance, L = 8N."""
+    out = []
+    for i in range(B):
+        snr = 20.0 * float(Stream(seed0 + i + 7919 * 1000003).uniform(1)[0])
+        out.append((make_mmv_instance(N, K, G, snr, seed0 + i), default_grid_size(N)))
+    return out
