@@ -169,6 +169,45 @@ def make_mmv_instance(N: int, K: int, G: int, snr_db: float, seed: int, *, law: 
                        snr_db=snr_db, seed=seed)
 
 
+@dataclasses.dataclass
+class IncompleteInstance:
+    y: np.ndarray  # complex64 [M]: the observed samples
+    obs: np.ndarray  # int32 [M]: their indices n_m in [0, N), ascending
+    N: int
+    theta: np.ndarray
+    alpha: np.ndarray
+    beta: float
+    snr_db: float
+    seed: int
+
+
+def draw_subset(stream: Stream, N: int, M: int) -> np.ndarray:
+    """M of the indices 0..N-1 uniformly without replacement (a partial
+    Fisher-Yates shuffle driven by the stream), ascending."""
+    idx = np.arange(N)
+    u = stream.uniform(M)
+    for i in range(M):
+        j = i + int(u[i] * (N - i))
+        idx[i], idx[j] = idx[j], idx[i]
+    return np.sort(idx[:M]).astype(np.int32)
+
+
+def make_incomplete_instance(N: int, M: int, K: int, snr_db: float, seed: int, *, law: str = "cn",
+                             min_sep: float | None = None) -> IncompleteInstance:
+    """The model of eq. (model) observed at M of its N samples (Phi a row
+    selection, Sec. IV): the signal and noise as make_instance, the SNR over
+    the observed samples, ||Phi Psi alpha||^2 / (M beta)."""
+    st = Stream(seed)
+    sep = (2.0 / N) if min_sep is None else min_sep
+    theta = draw_frequencies(st, K, sep)
+    alpha = draw_amplitudes(st, K, law)
+    obs = draw_subset(st, N, M)
+    h = sum_of_sinusoids(N, theta, alpha)[obs]
+    beta = float(np.vdot(h, h).real / (M * 10.0 ** (snr_db / 10.0))) if K else 1.0
+    y = (h + math.sqrt(beta) * st.cnormal(M)).astype(np.complex64)
+    return IncompleteInstance(y=y, obs=obs, N=N, theta=theta, alpha=alpha, beta=beta, snr_db=snr_db, seed=seed)
+
+
 def default_grid_size(N: int) -> int:
     """L = 8N rounded to the nearest power of two (Sec. II-D footnote)."""
     return 1 << int(round(math.log2(8 * N)))
@@ -250,3 +289,10 @@ def mmv_batch(seed0: int = 701, B: int = 64, N: int = 1024, G: int = 8, K: int =
         snr = 20.0 * float(Stream(seed0 + i + 7919 * 1000003).uniform(1)[0])
         out.append((make_mmv_instance(N, K, G, snr, seed0 + i), default_grid_size(N)))
     return out
+
+
+def incomplete_batch(seed0: int = 801, B: int = 64, N: int = 4096, M: int = 3072, K: int = 16):
+    """B instances observed at M = 3N/4 of N = 4096 samples (the paper's
+    incomplete-data setting, Sec. VI: a random subset, K = 16, 20 dB),
+    L = 4N."""
+    return [(make_incomplete_instance(N, M, K, 20.0, seed0 + i), 4 * N) for i in range(B)]
