@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -34,10 +35,70 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "batch64_n4096_k64_l16384"
+_T0 = time.perf_counter()
+
+
+def progress(msg: str) -> None:
+    """One progress line on stderr (the JSON result goes to stdout)."""
+    sys.stderr.write(f"[bench {time.perf_counter() - _T0:7.1f}s] {msg}\n")
+    sys.stderr.flush()
 METRIC = "grid-pt evals/s & fitted instances/s vs plain FP64 GPU path; serving p50/p99"
 B, N, K, L = 64, 4096, 64, 16384
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x DFMA/clk x 2 flop x max clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x 2 flop (FMA) x max clock
+
+
+def fft_flops(m: int) -> float:
+    """A complex FFT of length m counted as 5 m log2 m real flops (the radix-2 count)."""
+    return 5.0 * m * math.log2(m) if m > 1 else 0.0
+
+
+def pow2_at_least(x: int) -> int:
+    return 1 << max(0, int(x - 1).bit_length())
+
+
+def schur_flops(n: int, df: bool = True) -> float:
+    """Algorithmic flops of one superfast Schur factorisation of an n x n
+    Hermitian Toeplitz matrix as the recursion is structured (lse_schur.cuh):
+    a run of d > 32 orders splits into halves d1 = d/2, d2 = d - d1; with
+    M = pow2 >= d it costs 10 complex FFTs of length M (4 + 2 to form the
+    second half's windows, 2 + 2 to multiply the halves' 2x2 polynomial
+    matrices), or, for M <= 64 on the double-float path, direct sums of
+    2 (2 d2 (d1 + 1) + 2 (d + 1)(d2 + 1)) complex multiply-adds; a leaf of
+    d <= 32 orders ~2 d^2 + 2 d^2 multiply-adds (generator windows and the
+    two polynomial pairs); 8 flops per complex multiply-add; plus one step
+    of iterative refinement, 9 FFTs of length pow2 >= 2n."""
+    def run(d):
+        if d <= 32:
+            return 8.0 * 4 * d * d
+        d1 = d // 2
+        d2 = d - d1
+        M = pow2_at_least(d)
+        here = (8.0 * 2 * (2 * d2 * (d1 + 1) + 2 * (d + 1) * (d2 + 1))) if (df and M <= 64) else 10 * fft_flops(M)
+        return here + run(d1) + run(d2)
+    return run(n - 1) + 9 * fft_flops(pow2_at_least(2 * n))
+
+
+def eval_flops(n: int, k: int, g: int = 1, nufft_min_k: int = 32, df: bool = True) -> float:
+    """Algorithmic flops of one model evaluation on the default path: first
+    column (8 n k), superfast factorisation, one Gohberg-Semencul apply per
+    snapshot (5 FFTs of M2 = pow2 >= 2n, plus one shared), and the off-grid
+    sums at k frequencies (4 + 3 g sequences): directly 8 n k flops per
+    sequence, or by the non-uniform FFT (one FFT of M2 per sequence and a
+    16-point interpolation per frequency) when k >= nufft_min_k."""
+    m2 = pow2_at_least(2 * n)
+    nseq = 4 + 3 * g
+    if nufft_min_k and k >= nufft_min_k and n >= 64:
+        sums = nseq * (fft_flops(m2) + 8.0 * 16 * k)
+    else:
+        sums = nseq * 8.0 * n * k
+    return 8.0 * n * k + schur_flops(n, df) + (1 + 5 * g) * fft_flops(m2) + sums
+
+
+def grid_eval_flops(l: int, g: int = 1) -> float:
+    """One activation grid (Sec. III-D) in the fit: FFTs of the generator, its
+    index-weighted copy and x per snapshot, all of length l."""
+    return (2 + g) * fft_flops(l)
 
 
 def levinson_flops(n: int) -> float:
@@ -46,15 +107,6 @@ def levinson_flops(n: int) -> float:
     multiply-adds for the update and m for the next inner product (8 flops
     each) -> sum_m 16 m = 8 n^2."""
     return 8.0 * n * n
-
-
-def levinson_df_flops(n: int) -> float:
-    """FP32 flops of one double-float Levinson factorisation as implemented:
-    per pair (i, n-i) of an order, four double-float updates x + y1 z1 + y2 z2
-    (33 flops: two TwoProd-with-cross-terms of 7, two TwoSum of 6, four adds,
-    one Fast2Sum of 3) and eight product accumulations (15 flops) = 252 flops;
-    about n^2/4 pairs in all."""
-    return 252.0 * n * n / 4.0
 
 
 # DRAM traffic of fit_kernel<2> (dram__bytes_read.sum + dram__bytes_write.sum,
@@ -294,8 +346,13 @@ def _serve_run(lse, srv, pool, rate, seconds, admit_cap, drain_s, seed, rid0):
     i = 0
     t0 = _t.perf_counter()
     in_server = 0
+    next_report = 10.0
     while True:
         now = _t.perf_counter() - t0
+        if now >= next_report:
+            progress(f"serving {rate:.1f}/s: t={now:.0f}s arrivals={i} admitted={len(sub_t)} "
+                     f"completed={len(lat)} in_server={in_server}")
+            next_report += 10.0
         if now <= seconds:
             while i < len(times) and times[i] <= now:
                 fifo.append(i)
@@ -336,8 +393,8 @@ def serve_leg(lse, seconds, device):
     Payloads: the first SERVE_POOL requests of the stream, generated before
     any timing; arrival i carries payload i mod SERVE_POOL (sizes follow the
     stream's law).  Two phases of `seconds` each, on fresh servers whose
-    slots were first grown to the largest request (a noise-only signal of
-    that N, untimed): (1) the offered 2000 req/s with admission capped at
+    slots were first reserved (lse_serve_reserve, untimed) for full groups of
+    the largest request: (1) the offered 2000 req/s with admission capped at
     two requests per slot entry -- the server stays saturated, so its
     completions per second are the capacity, and the backlog grows; (2)
     Poisson arrivals at 80% of that capacity (latency at a sustainable
@@ -349,30 +406,29 @@ def serve_leg(lse, seconds, device):
     pool = [r.y for r in reqs]
     ns = _np.array([len(y) for y in pool])
     ks = _np.array([len(r.theta) for r in reqs])
-    noise = synth.make_instance(int(ns.max()), 0, 10.0, 9).y
     cfg = lse.lse_config_default(device=device, precision=lse.LSE_PREC_MIXED_DF, hbm_budget_bytes=40 << 30)
 
     def fresh():
         srv = lse.Server(cfg, streams=SERVE_STREAMS, max_group=SERVE_GROUP, K_cap=32768)
-        for k in range(SERVE_STREAMS * SERVE_GROUP):
-            srv.submit(noise, -1 - k)
-        got = 0
-        while got < SERVE_STREAMS * SERVE_GROUP:
-            got += len(srv.poll())
+        srv.reserve(int(ns.max()))
         return srv
 
+    progress("serving: growing the slots")
     srv = fresh()
+    progress("serving: offered 2000 req/s")
     try:
         overload = _serve_run(lse, srv, pool, 2000.0, seconds, 2 * SERVE_STREAMS * SERVE_GROUP, 15.0, 501,
                               30_000_000)
     finally:
         srv.close()
     capacity = overload["completed_in_window"] / seconds
+    progress(f"serving: capacity {capacity:.2f}/s; server closed")
     srv = fresh()
     try:
         sustained = _serve_run(lse, srv, pool, max(0.8 * capacity, 0.1), seconds, 1 << 30, 15.0, 502, 20_000_000)
     finally:
         srv.close()
+    progress("serving: done")
     return {"capacity_per_s": capacity, "offered_2000": overload, "sustained_80pct": sustained,
             "slots": SERVE_STREAMS, "max_group": SERVE_GROUP, "hbm_budget_gb": 40,
             "payload_pool": SERVE_POOL, "n_median": int(_np.median(ns)), "n_max": int(ns.max()),
@@ -467,6 +523,52 @@ def c3_grid_leg(lse, dev, steps, warmup, flush):
                               "bytes_per_launch": grid_bytes(Nc, Lc, False)}}
 
 
+def mmv_leg(lse, dev, steps, warmup, flush):
+    """Multiple measurement vectors (Sec. V): 64 instances of G = 8 snapshots,
+    N = 1024, K = 32 shared frequencies, SNR uniform on [0, 20] dB, L = 8N, one
+    launch of the fit kernel per step; the headline (double-float) path and the
+    plain FP64 path."""
+    import numpy as _np
+    import torch as _torch
+    from paper_1705_06073_gb300 import synth
+    work = synth.mmv_batch()
+    G = work[0][0].G
+    offs = _np.concatenate([[0], _np.cumsum([m.N for m, _ in work])]).astype(_np.int64)
+    y_d = _torch.from_numpy(_np.concatenate([m.Y.reshape(-1) for m, _ in work])).to(dev)
+    st = _torch.cuda.Stream(device=dev)
+    res = {}
+    for name, prec in (("mixed_df", lse.LSE_PREC_MIXED_DF), ("fp64", lse.LSE_PREC_FP64)):
+        ctx = lse.lse_create(lse.lse_config_default(device=dev.index or 0, precision=prec))
+        try:
+            out = lse.alloc_batch_out(offs, device=dev, G=G)
+            for _ in range(warmup):
+                lse.lse_fit_mmv_batch_d(ctx, y_d, offs, G, out, st)
+            st.synchronize()
+            lse.lse_kernel_time(ctx, 0)
+            ms = []
+            for _ in range(steps):
+                with _torch.cuda.stream(st):
+                    flush.zero_()
+                    e0 = _torch.cuda.Event(enable_timing=True)
+                    e1 = _torch.cuda.Event(enable_timing=True)
+                    e0.record(st)
+                    lse.lse_fit_mmv_batch_d(ctx, y_d, offs, G, out, st)
+                    e1.record(st)
+                st.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            kms, kl = lse.lse_kernel_time(ctx, 0)
+            res[name] = {"value": len(work) * steps / (sum(ms) / 1e3), "ms_per_step": sum(ms) / steps,
+                         "fit_kernel_ms": kms / max(kl, 1),
+                         "n_evals_mean": float(out["n_evals"].float().mean().item()),
+                         "K_mean": float(out["K"].float().mean().item()),
+                         "status_nonzero": int(_torch.count_nonzero(out["status"]).item())}
+        finally:
+            lse.lse_destroy(ctx)
+    return {"workload": f"mmv_batch64_n1024_g{G}_k32_l8192", "unit": "fitted instances/s",
+            "value": res["mixed_df"]["value"], "snapshots_per_instance": G, "paths": res,
+            "headline_over_fp64": res["mixed_df"]["value"] / res["fp64"]["value"]}
+
+
 # -------------------------------------------------------------- GPU arm ---
 def main():
     ap = argparse.ArgumentParser()
@@ -484,6 +586,7 @@ def main():
                     help="arrival window of each serving phase (80%% of capacity; 2000 req/s); 0 skips it")
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged 1024-instance graph launch")
     ap.add_argument("--no-c3", action="store_true", help="skip the N = 65536 eval-grid leg")
+    ap.add_argument("--no-mmv", action="store_true", help="skip the multiple-measurement-vector leg")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -564,6 +667,7 @@ def main():
     HEAD = names[0]
     ctxs = {}
     for name, prec in paths:
+        progress(f"fit leg {name}")
         ctx = lse.lse_create(lse.lse_config_default(device=local, precision=prec, grid_size=L))
         ctxs[name] = ctx
         out = lse.alloc_batch_out(offsets, device=dev)
@@ -582,6 +686,7 @@ def main():
                          n_evals=n_ev, n_grid=n_gr, status=st, K=Kf, iters=out["iters"].cpu().numpy(),
                          value=sum_over_ranks(Bn * args.steps) / (total_ms / 1e3), out=out)
 
+    progress("grid legs")
     # ---- grid-point throughput at the fitted states (factor + grid kernels)
     grid = {}
     for name, prec in paths:
@@ -629,6 +734,7 @@ def main():
         grid[name] = dict(value=sum_over_ranks(Bn * L * args.steps) / (tot / 1e3), ms=tot / args.steps,
                           factor_ms=fms / max(fl, 1), grid_ms=gms / max(gl, 1), launches=fl + gl)
 
+    progress("end-to-end leg")
     # ---- end to end through the host API (pinned host inputs, results back)
     ctx = ctxs[HEAD]
     if not args.no_e2e:
@@ -647,9 +753,14 @@ def main():
     for c in ctxs.values():
         lse.lse_destroy(c)
 
-    serving = serve_leg(lse, args.serve_seconds, local) if args.serve_seconds > 0 and rank == 0 else None
+    progress("ragged leg")
     ragged = ragged_leg(lse, dev) if not args.no_ragged and rank == 0 else None
+    progress("N = 65536 eval-grid leg")
     c3 = c3_grid_leg(lse, dev, args.steps, args.warmup, flush) if not args.no_c3 and rank == 0 else None
+    progress("multiple-measurement-vector leg")
+    mmv = mmv_leg(lse, dev, args.steps, args.warmup, flush) if not args.no_mmv and rank == 0 else None
+    progress("serving leg")
+    serving = serve_leg(lse, args.serve_seconds, local) if args.serve_seconds > 0 and rank == 0 else None
 
     if rank != 0:
         if dist:
@@ -657,17 +768,21 @@ def main():
         return
 
     m = res[HEAD]
-    # algorithmic flops of one launch (8 N^2 per factorisation of C, the
-    # recursion's count): every instance's evaluations in that fit
+    # algorithmic flops of one launch: every instance's evaluations (first
+    # column, superfast factorisation, Gohberg-Semencul apply, off-grid sums,
+    # with the instance's final K standing for the K of each evaluation) and
+    # activation grids
     kernel_s = m["kernel_ms"] / 1e3
-    fit_flops = float(np.sum(m["n_evals"])) * levinson_flops(N)
+    fit_flops = float(sum(int(ne) * eval_flops(N, int(k)) + int(ng) * grid_eval_flops(L)
+                          for ne, ng, k in zip(m["n_evals"], m["n_grid"], m["K"])))
     achieved = fit_flops / kernel_s / 1e12
-    df_instr = float(np.sum(m["n_evals"])) * levinson_df_flops(N) / kernel_s / 1e12
+    lev_equiv = float(np.sum(m["n_evals"])) * levinson_flops(N) / kernel_s / 1e12
     cpu = None
     if not args.no_cpu:
         threads = os.cpu_count() or 1
         try:
             counts = (float(np.mean(m["n_evals"])), float(np.mean(m["n_grid"])))
+            progress("CPU oracle sample")
             cpu = cpu_desc(oracle_sample(threads, counts=counts), threads)
         except Exception as e:  # the baseline is reported, never required
             cpu = {"value": None, "error": str(e)[:300]}
@@ -694,17 +809,22 @@ def main():
         "e2e": {"value": e2e_val, "unit": "fitted instances/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": fit_traffic(Bn),
-                     "kernel": "fit_kernel<2> (the generator recursion dominates; clusters of two blocks when 2B <= 152)",
-                     "algorithmic_flops": "8 N^2 per factorisation of C (the Levinson count) x factorisations in the launch",
+                     "kernel": "fit_kernel<2> (whole estimator; one block per instance)",
+                     "algorithmic_flops": ("per evaluation 8 N K (first column) + the superfast Schur count + "
+                                           "6 FFTs of 2N (Gohberg-Semencul) + the off-grid sums (direct 8 N K per "
+                                           "sequence, or non-uniform FFT for K >= 32); per grid 3 FFTs of L; a "
+                                           "length-M FFT = 5 M log2 M; the final K stands for each evaluation's"),
+                     "flops_per_launch": fit_flops,
                      "peak_source": "FP32 pipe, which the double-float kernel runs on: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived)",
                      "frac_of_fp64_pipe": achieved / FP64_PEAK_TFLOPS,
-                     "df_instruction_tflops": df_instr,
-                     "sms_busy": 2 * Bn if 2 * Bn <= 152 else min(Bn, 152)},
+                     "levinson_equivalent_tflops": lev_equiv,
+                     "sms_busy": min(Bn, 152)},
         "roofline_grid": {"bound": "hbm", "achieved": g_ach, "peak": peak_gbs, "unit": "GB/s",
                           "frac": g_ach / peak_gbs, "traffic": grid_traffic(Bn),
                           "kernel": "grid_fft_kernel<float> (a4+a5 of lse_eval_grid, all six outputs)",
                           "algorithmic_bytes": "(16 N + 36 L) per instance", "peak_source": peak_src},
         "c3_grid": c3,
+        "mmv": mmv,
         "fit": {"iters_mean": float(np.mean(m["iters"])), "n_evals_mean": float(np.mean(m["n_evals"])),
                 "n_grid_mean": float(np.mean(m["n_grid"])), "K_mean": float(np.mean(m["K"])),
                 "status_nonzero": int(np.count_nonzero(m["status"])), "fit_kernel_ms": m["kernel_ms"]},
@@ -718,7 +838,9 @@ def main():
     if "fp64" in res:
         f = res["fp64"]
         gf = grid["fp64"]
-        f_ach = float(np.sum(f["n_evals"])) * levinson_flops(N) / (f["kernel_ms"] / 1e3) / 1e12
+        f_flops = float(sum(int(ne) * eval_flops(N, int(k), df=False) + int(ng) * grid_eval_flops(L)
+                            for ne, ng, k in zip(f["n_evals"], f["n_grid"], f["K"])))
+        f_ach = f_flops / (f["kernel_ms"] / 1e3) / 1e12
         line["fp64_path"] = {"value": f["value"], "unit": "fitted instances/s", "ms_per_step": f["total_ms"] / args.steps,
                              "roofline": {"bound": "alu", "achieved": f_ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                                           "frac": f_ach / FP64_PEAK_TFLOPS},

@@ -114,6 +114,17 @@ typedef struct lse_config {
  * kappa(C). */
 #define LSE_FLAG_LEVINSON 4u
 
+/* Compute the off-grid sums of Sec. III-B/C (q, r, u at the active
+ * frequencies and the generator sums behind s, t, v, x; also the sums that
+ * re-score grid candidates) directly, O(N) per frequency, for every K.  By
+ * default a set of at least 32 frequencies (N >= 64) goes through a type-2
+ * non-uniform FFT instead (the route of the Sec. III-B footnote): the
+ * sequences divided by the transform of a Kaiser-Bessel kernel of width 16,
+ * one batched FFT of M >= 2N points, and a 16-point interpolation per
+ * frequency, O(N log N + 16 K); its error is near the FFT's own rounding
+ * (about 1e-14 of sum |f_n|). */
+#define LSE_FLAG_DIRECT_SUMS 8u
+
 /* Fill cfg with the paper's defaults (device 0, FP64, tau = 5, ...). */
 LSE_API void lse_config_default(lse_config* cfg);
 
@@ -194,6 +205,40 @@ LSE_API lse_status lse_fit_batch(lse_ctx* ctx, const float* y, const int64_t* of
 LSE_API lse_status lse_fit_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* offsets, int32_t B,
                            const lse_batch_out* out, void* stream);
 
+/* ---- Multiple measurement vectors (Sec. V) ---------------------------------
+ * G snapshots y^(1), ..., y^(G) of one instance share the frequencies, the
+ * variances gamma, the noise variance and the activation probability, hence
+ * one covariance C (eq. py); each snapshot has its own coefficients.  The fit
+ * minimises G ln|C| + sum_g y_g^H C^{-1} y_g minus the prior term (eq. L_MMV):
+ * one factorisation of C per evaluation serves every snapshot, while the
+ * Gohberg-Semencul apply, the q, r, u sums and the q grid run per snapshot.
+ * The derivatives are sums over snapshots (Sec. V); activation and
+ * deactivation use Q = sum_g |q_g|^2 in eq. (singlecomp-mmv): gamma-hat =
+ * (Q/G - s)/s^2, Delta L = G ln(1 + gb s) + ln((1-zeta)/zeta) - gb Q/(1 + gb s),
+ * the activation test Q/(G s) > (1 + 1/(gb s)) (ln(1 + gb s) + ln((1-zeta)/zeta)/G)
+ * + tau, and the removal test gamma Q~/(1 + gamma s~) - G ln(1 + gamma s~) <
+ * ln((1-zeta)/zeta); beta averages the residual term over snapshots; the
+ * initial beta, eps_beta and the termination and Newton-decrement thresholds
+ * scale with G N.  With G = 1 every rule is the single-snapshot one and the
+ * results equal lse_fit's bit for bit. */
+
+/* Fit one instance of G snapshots.  y: host complex64, G x N snapshot-major
+ * (snapshot g at y[2 g N .. 2 (g+1) N)); 2 <= N <= 131072, 1 <= G <= 1024.
+ * out->alpha holds K_cap x G complex values: snapshot g's coefficient of
+ * component k at alpha[2 (g K_cap + k)] (eq. bmu with y replaced by y^(g));
+ * theta and gamma as for lse_fit.  Blocks until the result is in out. */
+LSE_API lse_status lse_fit_mmv(lse_ctx* ctx, const float* y, int32_t N, int32_t G, lse_result* out);
+
+/* Batched device-pointer fit of B instances of G snapshots each (G the same
+ * for the whole batch, N ragged).  offsets: HOST [B+1] in samples per
+ * snapshot, as for lse_fit_batch_d; instance b's snapshot g starts at complex
+ * element G offsets[b] + g N_b of y_d.  out: as lse_batch_out, except that
+ * alpha holds 2 G sum N_b doubles: instance b's snapshot g's coefficient of
+ * its k-th component at complex element G offsets[b] + g N_b + k.  The
+ * asynchrony and stream-capture rules of lse_fit_batch_d apply. */
+LSE_API lse_status lse_fit_mmv_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* offsets, int32_t B,
+                                       int32_t G, const lse_batch_out* out, void* stream);
+
 /* ---- Planned batches and CUDA graphs ----------------------------------
  * A plan fixes the shape of a batched fit (offsets, B) and owns its device
  * workspace, so that a launch enqueues device work only (a counter reset and
@@ -269,6 +314,17 @@ LSE_API int32_t lse_serve_in_flight(const lse_server* s);
 
 /* Device memory the running groups hold, in bytes (the budgeted quantity). */
 LSE_API uint64_t lse_serve_device_bytes(const lse_server* s);
+
+/* Grow every slot's device buffers and fit workspace, once, for a full group
+ * of max_group requests of up to n_max samples each (L = cfg->grid_size, or
+ * 8 n_max rounded to the nearest power of two).  A slot otherwise grows when
+ * a larger group first reaches it, and releasing device memory waits for
+ * every fit running on the device, which stalls lse_serve_poll and the whole
+ * admission loop behind the longest running group.  Call it before traffic
+ * starts; it waits for the slots' running groups (their results stay
+ * queued for lse_serve_poll) and for the device.  The reserved memory is not
+ * counted against hbm_budget_bytes, which budgets running groups. */
+LSE_API lse_status lse_serve_reserve(lse_server* s, int32_t n_max);
 
 /* Wait for running groups and release everything.  NULL is accepted. */
 LSE_API void lse_serve_destroy(lse_server* s);

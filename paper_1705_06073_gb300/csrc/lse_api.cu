@@ -74,6 +74,9 @@ struct lse_plan {
 
 namespace {
 
+// snapshots per instance accepted by the multiple-measurement-vector fits
+constexpr int32_t kMaxSnapshots = 1024;
+
 lse_status fail(lse_ctx* c, lse_status s, const std::string& msg) {
   if (c) c->err = msg;
   return s;
@@ -215,6 +218,14 @@ lse_status order_after(lse_ctx* c, cudaStream_t waiter, cudaStream_t done) {
 
 void record(lse_ctx* c, int which, cudaStream_t st, bool start) {
   if (is_capturing(st)) return;  // events recorded into a graph carry no time
+  if (start && c->timed[which].size() >= 4096) {  // nobody reads them (a server's slot): keep the newest half
+    auto& v = c->timed[which];
+    for (size_t i = 0; i < v.size() / 2; ++i) {
+      cudaEventDestroy(v[i].a);
+      cudaEventDestroy(v[i].b);
+    }
+    v.erase(v.begin(), v.begin() + v.size() / 2);
+  }
   if (start) {
     TimedLaunch t;
     cudaEventCreate(&t.a);
@@ -281,6 +292,31 @@ lse_status plan_fit_descs(lse_ctx* ctx, const int64_t* offsets, int32_t B, std::
 
 cudaStream_t lse_ctx_stream(lse_ctx* c) { return c ? c->stream : nullptr; }
 
+lse_status lse_ctx_reserve_fit(lse_ctx* ctx, int Nmax, int Lmax, int B) {
+  if (!ctx || Nmax < 2 || Lmax < 2 * Nmax || B < 1) return LSE_EINVAL;
+  cudaSetDevice(ctx->cfg.device);
+  lse_status s;
+  if ((s = ensure_tables(ctx, std::max(ilog2((uint32_t)Lmax), ilog2(2u * (uint32_t)Nmax))))) return s;
+  const int grid = std::min(B, ctx->sm_count);
+  if ((s = ensure(ctx, ctx->ws, fit_workspace_bytes(Nmax, Lmax, ctx->cfg.precision) * grid))) return s;
+  const size_t db = (size_t)B * sizeof(InstDesc);
+  if ((s = ensure(ctx, ctx->fit_meta.dev, db))) return s;
+  Staged& st = ctx->fit_meta;
+  for (int k = 0; k < 2; ++k) {
+    if (!st.ev[k]) LSE_CUDA(ctx, cudaEventCreateWithFlags(&st.ev[k], cudaEventDisableTiming));
+    if (st.pcap[k] < db) {
+      LSE_CUDA(ctx, cudaEventSynchronize(st.ev[k]));
+      if (st.pinned[k]) cudaFreeHost(st.pinned[k]);
+      st.pinned[k] = nullptr;
+      st.pcap[k] = 0;
+      LSE_CUDA(ctx, cudaMallocHost((void**)&st.pinned[k], db));
+      st.pcap[k] = db;
+    }
+  }
+  LSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return LSE_OK;
+}
+
 extern "C" {
 
 void lse_config_default(lse_config* cfg) {
@@ -321,7 +357,7 @@ lse_status lse_create(const lse_config* cfg, lse_ctx** out) {
   if (c.precision != LSE_PREC_FP64 && c.precision != LSE_PREC_MIXED && c.precision != LSE_PREC_MIXED_DF)
     return LSE_EINVAL;
   if (c.max_outer < 1 || c.max_inner < 0 || c.approx_activation_iters < 0 || !(c.tau >= 0.0) ||
-      (c.flags & ~(uint64_t)(LSE_FLAG_NO_AUTOTUNE | LSE_FLAG_NO_CLUSTER | LSE_FLAG_LEVINSON)))
+      (c.flags & ~(uint64_t)(LSE_FLAG_NO_AUTOTUNE | LSE_FLAG_NO_CLUSTER | LSE_FLAG_LEVINSON | LSE_FLAG_DIRECT_SUMS)))
     return LSE_EINVAL;
   if (c.grid_size < 0 || (c.grid_size > 0 && !is_pow2(c.grid_size))) return LSE_EINVAL;
   int ndev = 0;
@@ -381,9 +417,16 @@ lse_status lse_kernel_time(lse_ctx* ctx, int32_t which, double* total_ms, int64_
   return LSE_OK;
 }
 
-lse_status lse_fit_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* offsets, int32_t B,
-                           const lse_batch_out* out, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// Batched fit of B instances with G snapshots each (G = 1: lse_fit_batch_d;
+// G > 1: lse_fit_mmv_batch_d).
+lse_status fit_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* offsets, int32_t B, int32_t G,
+                       const lse_batch_out* out, void* stream) {
   if (!ctx || !y_d || !offsets || B < 1 || !out) return fail(ctx, LSE_EINVAL, "null argument or B < 1");
+  if (G < 1 || G > kMaxSnapshots) return fail(ctx, LSE_EINVAL, "G out of range");
   if (offsets[0] != 0) return fail(ctx, LSE_EINVAL, "offsets[0] must be 0");
   cudaSetDevice(ctx->cfg.device);
   cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
@@ -398,13 +441,14 @@ lse_status lse_fit_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* offset
     return fail(ctx, LSE_EINVAL, "twiddle tables must grow, which cannot be captured: make one call first");
   if ((s = ensure_tables(ctx, log2t))) return s;
   const int grid = std::min(B, ctx->sm_count);
-  const size_t per = fit_workspace_bytes(Nmax, Lmax, prec);
+  const size_t per = fit_workspace_bytes(Nmax, Lmax, prec, G);
   if ((s = ensure(ctx, ctx->ws, per * grid, cap))) return s;
   if (!cap && st != ctx->stream && (s = order_after(ctx, st, ctx->stream))) return s;
   if ((s = stage(ctx, ctx->fit_meta, d.data(), d.size() * sizeof(InstDesc), st, cap))) return s;
   LSE_CUDA(ctx, cudaMemsetAsync(ctx->counter.p, 0, sizeof(int), st));
   FitConfig fc{ctx->cfg.tau, ctx->cfg.max_outer, ctx->cfg.max_inner, ctx->cfg.approx_activation_iters,
-               !(ctx->cfg.flags & LSE_FLAG_NO_CLUSTER), superfast_min_n(ctx->cfg.flags), Nmin};
+               !(ctx->cfg.flags & LSE_FLAG_NO_CLUSTER), superfast_min_n(ctx->cfg.flags), Nmin, G,
+               nufft_min_k(ctx->cfg.flags)};
   FitOut fo{out->theta, out->gamma, (c128*)out->alpha, out->K, out->beta, out->objective, out->iters,
             out->n_evals, out->n_grid, out->status};
   record(ctx, 0, st, true);
@@ -415,6 +459,101 @@ lse_status lse_fit_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* offset
   // later work of this context on its own stream must follow this launch
   if (!cap && st != ctx->stream && (s = order_after(ctx, ctx->stream, st))) return s;
   return LSE_OK;
+}
+
+// Host-array batched fit with G snapshots per instance: stage y in, run
+// fit_batch_d, copy the results back and unpack them per instance.
+lse_status fit_batch_host(lse_ctx* ctx, const float* y, const int64_t* offsets, int32_t B, int32_t G,
+                          lse_result* outs, lse_status* per_instance) {
+  if (!ctx || !y || !offsets || B < 1 || !outs) return fail(ctx, LSE_EINVAL, "null argument or B < 1");
+  if (G < 1 || G > kMaxSnapshots) return fail(ctx, LSE_EINVAL, "G out of range");
+  cudaSetDevice(ctx->cfg.device);
+  const int64_t tot = offsets[B];
+  if (tot <= 0) return fail(ctx, LSE_EINVAL, "empty batch");
+  // device staging: y | theta | gamma | alpha | K | beta | obj | iters | nevals | status
+  const size_t yb = (size_t)tot * G * 2 * sizeof(float);
+  const size_t ob = (size_t)tot * (2 + 2 * G) * sizeof(double) + (size_t)B * (5 * sizeof(int) + 2 * sizeof(double)) +
+                    1024;
+  lse_status s;
+  if ((s = ensure(ctx, ctx->stage_in, yb))) return s;
+  if ((s = ensure(ctx, ctx->stage_out, ob))) return s;
+  char* o = (char*)ctx->stage_out.p;
+  lse_batch_out bo;
+  bo.theta = (double*)o; o += tot * sizeof(double);
+  bo.gamma = (double*)o; o += tot * sizeof(double);
+  bo.alpha = (double*)o; o += tot * G * 2 * sizeof(double);
+  bo.beta = (double*)o; o += B * sizeof(double);
+  bo.objective = (double*)o; o += B * sizeof(double);
+  bo.K = (int32_t*)o; o += B * sizeof(int);
+  bo.iters = (int32_t*)o; o += B * sizeof(int);
+  bo.n_evals = (int32_t*)o; o += B * sizeof(int);
+  bo.n_grid = (int32_t*)o; o += B * sizeof(int);
+  bo.status = (int32_t*)o; o += B * sizeof(int);
+  LSE_CUDA(ctx, cudaMemcpyAsync(ctx->stage_in.p, y, yb, cudaMemcpyHostToDevice, ctx->stream));
+  if ((s = fit_batch_d(ctx, (const float*)ctx->stage_in.p, offsets, B, G, &bo, ctx->stream))) return s;
+  std::vector<char> host(ob);
+  LSE_CUDA(ctx, cudaMemcpyAsync(host.data(), ctx->stage_out.p, ob, cudaMemcpyDeviceToHost, ctx->stream));
+  LSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const char* h = host.data();
+  const double* th = (const double*)h;
+  const double* ga = th + tot;
+  const double* al = ga + tot;
+  const double* be = al + 2 * G * tot;
+  const double* ob_ = be + B;
+  const int32_t* K = (const int32_t*)(ob_ + B);
+  const int32_t* it = K + B;
+  const int32_t* ne = it + B;
+  const int32_t* ng = ne + B;
+  const int32_t* stt = ng + B;
+  for (int b = 0; b < B; ++b) {
+    lse_result& r = outs[b];
+    lse_status sb = (lse_status)stt[b];
+    r.K = K[b];
+    r.beta = be[b];
+    r.objective = ob_[b];
+    r.iters = it[b];
+    r.n_evals = ne[b];
+    r.n_grid = ng[b];
+    if (K[b] > r.K_cap) {
+      sb = LSE_ECAPACITY;
+    } else {
+      const int64_t off = offsets[b], Nb = offsets[b + 1] - offsets[b];
+      for (int k = 0; k < K[b]; ++k) {
+        if (r.theta) r.theta[k] = th[off + k];
+        if (r.gamma) r.gamma[k] = ga[off + k];
+        if (r.alpha)
+          for (int g = 0; g < G; ++g) {
+            const int64_t src = 2 * ((int64_t)G * off + g * Nb + k), dst = 2 * ((int64_t)g * r.K_cap + k);
+            r.alpha[dst] = al[src];
+            r.alpha[dst + 1] = al[src + 1];
+          }
+      }
+    }
+    if (per_instance) per_instance[b] = sb;
+  }
+  return LSE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lse_status lse_fit_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* offsets, int32_t B,
+                           const lse_batch_out* out, void* stream) {
+  return fit_batch_d(ctx, y_d, offsets, B, 1, out, stream);
+}
+
+lse_status lse_fit_mmv_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* offsets, int32_t B, int32_t G,
+                               const lse_batch_out* out, void* stream) {
+  return fit_batch_d(ctx, y_d, offsets, B, G, out, stream);
+}
+
+lse_status lse_fit_mmv(lse_ctx* ctx, const float* y, int32_t N, int32_t G, lse_result* out) {
+  if (!ctx || !y || !out || N < 2) return fail(ctx, LSE_EINVAL, "null argument or N < 2");
+  const int64_t off[2] = {0, N};
+  lse_status per = LSE_OK;
+  lse_status s = fit_batch_host(ctx, y, off, 1, G, out, &per);
+  return s ? s : per;
 }
 
 lse_status lse_plan_fit(lse_ctx* ctx, const int64_t* offsets, int32_t B, lse_plan** out) {
@@ -453,7 +592,8 @@ lse_status lse_plan_launch(lse_plan* p, const float* y_d, const lse_batch_out* o
   cudaStream_t st = (cudaStream_t)stream;
   LSE_CUDA(ctx, cudaMemsetAsync(p->counter.p, 0, sizeof(int), st));
   const FitConfig fc{ctx->cfg.tau, ctx->cfg.max_outer, ctx->cfg.max_inner, ctx->cfg.approx_activation_iters,
-                     !(ctx->cfg.flags & LSE_FLAG_NO_CLUSTER), superfast_min_n(ctx->cfg.flags), p->Nmin};
+                     !(ctx->cfg.flags & LSE_FLAG_NO_CLUSTER), superfast_min_n(ctx->cfg.flags), p->Nmin, 1,
+                     nufft_min_k(ctx->cfg.flags)};
   const FitOut fo{out->theta, out->gamma, (c128*)out->alpha, out->K, out->beta, out->objective, out->iters,
                   out->n_evals, out->n_grid, out->status};
   const cudaError_t e = launch_fit(p->prec, y_d, (const InstDesc*)p->desc.p, p->B, p->Nmax, p->Lmax, fc, tables(ctx),
@@ -507,66 +647,7 @@ void lse_plan_destroy(lse_plan* p) {
 
 lse_status lse_fit_batch(lse_ctx* ctx, const float* y, const int64_t* offsets, int32_t B, lse_result* outs,
                          lse_status* per_instance) {
-  if (!ctx || !y || !offsets || B < 1 || !outs) return fail(ctx, LSE_EINVAL, "null argument or B < 1");
-  cudaSetDevice(ctx->cfg.device);
-  const int64_t tot = offsets[B];
-  if (tot <= 0) return fail(ctx, LSE_EINVAL, "empty batch");
-  // device staging: y | theta | gamma | alpha | K | beta | obj | iters | nevals | status
-  const size_t yb = (size_t)tot * 2 * sizeof(float);
-  const size_t ob = (size_t)tot * (2 + 2) * sizeof(double) + (size_t)B * (5 * sizeof(int) + 2 * sizeof(double)) + 1024;
-  lse_status s;
-  if ((s = ensure(ctx, ctx->stage_in, yb))) return s;
-  if ((s = ensure(ctx, ctx->stage_out, ob))) return s;
-  char* o = (char*)ctx->stage_out.p;
-  lse_batch_out bo;
-  bo.theta = (double*)o; o += tot * sizeof(double);
-  bo.gamma = (double*)o; o += tot * sizeof(double);
-  bo.alpha = (double*)o; o += tot * 2 * sizeof(double);
-  bo.beta = (double*)o; o += B * sizeof(double);
-  bo.objective = (double*)o; o += B * sizeof(double);
-  bo.K = (int32_t*)o; o += B * sizeof(int);
-  bo.iters = (int32_t*)o; o += B * sizeof(int);
-  bo.n_evals = (int32_t*)o; o += B * sizeof(int);
-  bo.n_grid = (int32_t*)o; o += B * sizeof(int);
-  bo.status = (int32_t*)o; o += B * sizeof(int);
-  LSE_CUDA(ctx, cudaMemcpyAsync(ctx->stage_in.p, y, yb, cudaMemcpyHostToDevice, ctx->stream));
-  if ((s = lse_fit_batch_d(ctx, (const float*)ctx->stage_in.p, offsets, B, &bo, ctx->stream))) return s;
-  std::vector<char> host(ob);
-  LSE_CUDA(ctx, cudaMemcpyAsync(host.data(), ctx->stage_out.p, ob, cudaMemcpyDeviceToHost, ctx->stream));
-  LSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  const char* h = host.data();
-  const double* th = (const double*)h;
-  const double* ga = th + tot;
-  const double* al = ga + tot;
-  const double* be = al + 2 * tot;
-  const double* ob_ = be + B;
-  const int32_t* K = (const int32_t*)(ob_ + B);
-  const int32_t* it = K + B;
-  const int32_t* ne = it + B;
-  const int32_t* ng = ne + B;
-  const int32_t* stt = ng + B;
-  for (int b = 0; b < B; ++b) {
-    lse_result& r = outs[b];
-    lse_status sb = (lse_status)stt[b];
-    r.K = K[b];
-    r.beta = be[b];
-    r.objective = ob_[b];
-    r.iters = it[b];
-    r.n_evals = ne[b];
-    r.n_grid = ng[b];
-    if (K[b] > r.K_cap) {
-      sb = LSE_ECAPACITY;
-    } else {
-      const int64_t off = offsets[b];
-      for (int k = 0; k < K[b]; ++k) {
-        if (r.theta) r.theta[k] = th[off + k];
-        if (r.gamma) r.gamma[k] = ga[off + k];
-        if (r.alpha) { r.alpha[2 * k] = al[2 * (off + k)]; r.alpha[2 * k + 1] = al[2 * (off + k) + 1]; }
-      }
-    }
-    if (per_instance) per_instance[b] = sb;
-  }
-  return LSE_OK;
+  return fit_batch_host(ctx, y, offsets, B, 1, outs, per_instance);
 }
 
 lse_status lse_fit(lse_ctx* ctx, const float* y, int32_t N, lse_result* out) {

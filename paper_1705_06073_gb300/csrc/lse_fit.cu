@@ -34,6 +34,7 @@
 #include "lse_device.cuh"
 #include "lse_df64.cuh"
 #include "lse_internal.h"
+#include "lse_nufft.cuh"
 #include "lse_schur.cuh"
 
 namespace lse {
@@ -52,6 +53,8 @@ constexpr int kST_OK = 0, kST_NUMERIC = 4, kST_NOTCONV = 5;
 constexpr int kBigCluster = 8;
 // smallest N that uses the superfast Schur recursion by default
 constexpr int kSuperfastMinN = 64;
+// fewest frequencies whose off-grid sums go through the non-uniform FFT by default
+constexpr int kNufftMinK = 32;
 
 // whether the recursion's c and a (2N complex doubles) and the first-column
 // tables fit in the block's dynamic shared memory
@@ -79,29 +82,42 @@ struct FitShared {
   // grid decisions of the mixed paths: best FP32 candidates re-scored in FP64
   int ntop, sel;
   int top[32];
-  double top_dl[32], top_s[32];
-  c128 top_q[32];
+  double top_dl[32], top_s[32], top_Q[32];
 };
 
-// Per-block global workspace for an instance of size up to (Nmax, Lmax).
+// Per-block global workspace for an instance of size up to (Nmax, Lmax) with
+// G snapshots (Sec. V; G = 1 for a single measurement vector).  Per-snapshot
+// arrays hold snapshot g at g * (their per-snapshot stride).
 template <class TG>
 struct Work {
+  int ny, nyf;      // per-snapshot strides: Nmax (y, x, x_df, 7 Nmax for sums), M2max (Yf)
   c128 *y, *c, *a, *rho, *x, *Yf;
   c128* buf[5];     // FFT buffers, M2max each (GS apply)
   cx<TG>* gbuf[4];  // grid FFT buffers, Lmax each
   double *theta, *gamma, *th_t, *ga_t, *dth, *dga;
-  c128* sums;       // 7 * Nmax off-grid sums (FP64 on every path)
-  float4 *rho_df, *x_df;  // Nmax each: rho and x as double-float pairs (double-float path)
+  c128* sums;       // G x 7 Nmax off-grid sums (FP64 on every path)
+  float4 *rho_df, *x_df;  // Nmax and G x Nmax: rho and x as double-float pairs (double-float path)
   double* dl;       // Lmax
   int* cand;        // Lmax
   double *cand_dl, *cand_s;  // Lmax: decision values of the candidates
-  c128* cand_q;     // Lmax
+  double* cand_Q;   // Lmax: sum over snapshots of |q|^2 at the candidates
   double* rs_theta;  // kRescore: frequencies being re-scored
-  c128* rs_sums;     // 7 * kRescore
+  c128* rs_sums;     // G x 7 kRescore
   float4* sf;        // superfast Schur recursion (schur_workspace_elems(Nmax))
+  double* gq2;       // Lmax: sum over snapshots of |q|^2 on the grid (G > 1)
+  float4* nu;        // 2 (4 + 3G) M2max: transforms of the non-uniform FFT sums
+  double* nfac64;    // Nmax: its deconvolution factors (FP64)
+  float2* nfacdf;    // Nmax: the same as double-float pairs
+  __device__ c128* yg(int g) const { return y + (size_t)g * ny; }
+  __device__ c128* xg(int g) const { return x + (size_t)g * ny; }
+  __device__ c128* Yfg(int g) const { return Yf + (size_t)g * nyf; }
+  __device__ float4* xdfg(int g) const { return x_df + (size_t)g * ny; }
+  __device__ c128* sumsg(int g) const { return sums + (size_t)g * 7 * ny; }
+  __device__ c128* rssumsg(int g) const { return rs_sums + (size_t)g * 7 * kRescoreW; }
+  static constexpr int kRescoreW = 1024;
 };
 
-constexpr int kRescore = 1024;  // grid points re-scored in FP64 per batch
+constexpr int kRescore = Work<double>::kRescoreW;  // grid points re-scored in FP64 per batch
 
 struct Layout {
   size_t off[40];
@@ -109,36 +125,45 @@ struct Layout {
 };
 
 template <class TG>
-__host__ __device__ inline Layout make_layout(int Nmax, int Lmax) {
+__host__ __device__ inline Layout make_layout(int Nmax, int Lmax, int G) {
   Layout L;
   const int M2 = 1 << ilog2(2u * (uint32_t)Nmax);
   size_t o = 0;
   int i = 0;
   auto put = [&](size_t bytes) { L.off[i++] = o; o += (bytes + 255) & ~size_t(255); };
-  for (int j = 0; j < 6; ++j) put(sizeof(c128) * (size_t)Nmax);       // y c a rho x (+1 spare)
-  put(sizeof(c128) * (size_t)M2);                                       // Yf
+  put(sizeof(c128) * (size_t)Nmax * G);                                 // y
+  for (int j = 0; j < 3; ++j) put(sizeof(c128) * (size_t)Nmax);       // c a rho
+  put(sizeof(c128) * (size_t)Nmax * G);                                 // x
+  put(sizeof(c128) * (size_t)Nmax);                                     // (spare)
+  put(sizeof(c128) * (size_t)M2 * G);                                   // Yf
   for (int j = 0; j < 5; ++j) put(sizeof(c128) * (size_t)M2);          // buf
   for (int j = 0; j < 4; ++j) put(sizeof(cx<TG>) * (size_t)Lmax);      // gbuf
   for (int j = 0; j < 6; ++j) put(sizeof(double) * (size_t)Nmax);      // theta..dga
-  put(sizeof(c128) * 7 * (size_t)Nmax);                                 // sums
+  put(sizeof(c128) * 7 * (size_t)Nmax * G);                             // sums
   put(sizeof(float4) * (size_t)Nmax);                                   // rho_df
-  put(sizeof(float4) * (size_t)Nmax);                                   // x_df
+  put(sizeof(float4) * (size_t)Nmax * G);                               // x_df
   put(sizeof(double) * (size_t)Lmax);                                   // dl
   put(sizeof(int) * (size_t)Lmax);                                      // cand
   put(sizeof(double) * (size_t)Lmax);                                   // cand_dl
   put(sizeof(double) * (size_t)Lmax);                                   // cand_s
-  put(sizeof(c128) * (size_t)Lmax);                                     // cand_q
+  put(sizeof(double) * (size_t)Lmax);                                   // cand_Q
   put(sizeof(double) * (size_t)kRescore);                               // rs_theta
-  put(sizeof(c128) * 7 * (size_t)kRescore);                             // rs_sums
+  put(sizeof(c128) * 7 * (size_t)kRescore * G);                         // rs_sums
   put(sizeof(float4) * schur_workspace_elems(Nmax));                     // sf
+  put(G > 1 ? sizeof(double) * (size_t)Lmax : 0);                       // gq2
+  put(sizeof(float4) * 2 * (size_t)(4 + 3 * G) * M2);                   // nu
+  put(sizeof(double) * (size_t)Nmax);                                   // nfac64
+  put(sizeof(float2) * (size_t)Nmax);                                   // nfacdf
   L.total = o;
   return L;
 }
 
 template <class TG>
-__device__ Work<TG> carve(char* base, int Nmax, int Lmax) {
-  Layout L = make_layout<TG>(Nmax, Lmax);
+__device__ Work<TG> carve(char* base, int Nmax, int Lmax, int G) {
+  Layout L = make_layout<TG>(Nmax, Lmax, G);
   Work<TG> w;
+  w.ny = Nmax;
+  w.nyf = 1 << ilog2(2u * (uint32_t)Nmax);
   int i = 0;
   w.y = (c128*)(base + L.off[i++]);
   w.c = (c128*)(base + L.off[i++]);
@@ -162,10 +187,14 @@ __device__ Work<TG> carve(char* base, int Nmax, int Lmax) {
   w.cand = (int*)(base + L.off[i++]);
   w.cand_dl = (double*)(base + L.off[i++]);
   w.cand_s = (double*)(base + L.off[i++]);
-  w.cand_q = (c128*)(base + L.off[i++]);
+  w.cand_Q = (double*)(base + L.off[i++]);
   w.rs_theta = (double*)(base + L.off[i++]);
   w.rs_sums = (c128*)(base + L.off[i++]);
   w.sf = (float4*)(base + L.off[i++]);
+  w.gq2 = (double*)(base + L.off[i++]);
+  w.nu = (float4*)(base + L.off[i++]);
+  w.nfac64 = (double*)(base + L.off[i++]);
+  w.nfacdf = (float2*)(base + L.off[i++]);
   return w;
 }
 
@@ -209,6 +238,8 @@ struct Fitter {
   Work<TG> w;
   const FitArgs* A;
   int N, L, log2L, log2M2;
+  int G;      // snapshots of the instance (Sec. V); 1 for a single measurement vector
+  double Gd;  // G as a double
   bool lev_smem;
   c128 *lev_c, *lev_a, *tables;
   float4* sf_smem;  // superfast recursion: its shared-memory part (after the tables)
@@ -247,30 +278,40 @@ struct Fitter {
     for (int n = threadIdx.x; n < N; n += kNT) w.rho[n] = conj(lev_a[N - 1 - n]);
     __syncthreads();
     c128* bufs[5] = {w.buf[0], w.buf[1], w.buf[2], w.buf[3], w.buf[4]};
-    bool gs_done = false;
-    if constexpr (PREC == 2) {  // double-float transforms when the table exists
-      if (A->tab.twdf) {
-        block_gs_apply_df<kNT>(w.rho, w.Yf, w.x, N, log2M2, lr.delta_last, bufs,
-                               TwiddlesDF{A->tab.twdf, A->tab.log2max});
-        gs_done = true;
-      }
-    }
-    if (!gs_done) block_gs_apply<kNT>(w.rho, w.Yf, w.x, N, log2M2, lr.delta_last, bufs, tw64);
     double part = 0.0;
-    for (int n = threadIdx.x; n < N; n += kNT) part += (conj(w.y[n]) * w.x[n]).re;
+    for (int g = 0; g < G; ++g) {  // x_g = C^{-1} y_g, one Gohberg-Semencul apply per snapshot
+      bool gs_done = false;
+      if constexpr (PREC == 2) {  // double-float transforms when the table exists
+        if (A->tab.twdf) {
+          block_gs_apply_df<kNT>(w.rho, w.Yfg(g), w.xg(g), N, log2M2, lr.delta_last, bufs,
+                                 TwiddlesDF{A->tab.twdf, A->tab.log2max});
+          gs_done = true;
+        }
+      }
+      if (!gs_done) block_gs_apply<kNT>(w.rho, w.Yfg(g), w.xg(g), N, log2M2, lr.delta_last, bufs, tw64);
+      const c128 *yv = w.yg(g), *xv = w.xg(g);
+      for (int n = threadIdx.x; n < N; n += kNT) part += (conj(yv[n]) * xv[n]).re;
+    }
     const double yCy = block_sum<kNT>(part, sh->dred);
     if (threadIdx.x == 0) {
       sh->logdet = lr.logdet;
       sh->yCy = yCy;
       sh->delta_last = lr.delta_last;
-      sh->f_cur = lr.logdet + yCy;
+      sh->f_cur = Gd * lr.logdet + yCy;  // eq. (obj); G ln|C| + sum_g y_g^H C^{-1} y_g for G snapshots (Sec. V)
     }
     __syncthreads();
     if constexpr (PREC == 2) {  // double-float copies for the sums
       for (int n = threadIdx.x; n < N; n += kNT) {
-        const c128 r = w.rho[n], v = w.x[n];
+        const c128 r = w.rho[n];
         w.rho_df[n] = pack(to_f2(r.re), to_f2(r.im));
-        w.x_df[n] = pack(to_f2(v.re), to_f2(v.im));
+      }
+      for (int g = 0; g < G; ++g) {
+        const c128* xv = w.xg(g);
+        float4* xd = w.xdfg(g);
+        for (int n = threadIdx.x; n < N; n += kNT) {
+          const c128 v = xv[n];
+          xd[n] = pack(to_f2(v.re), to_f2(v.im));
+        }
       }
       __syncthreads();
     }
@@ -326,8 +367,28 @@ struct Fitter {
   // directions disagree with the FP64 objective and the line search stalls.
   __device__ void compute_sums(const double* th, int K) {
     if (K <= 0) return;
-    if constexpr (PREC == 2) block_active_sums_df<kNT>(w.rho_df, w.x_df, th, K, N, w.sums);
-    else block_active_sums<kNT, double>(w.rho, w.x, th, K, N, w.sums);
+    if (use_nufft(K)) {
+      sums_nufft(th, K, w.sums, 7 * (size_t)w.ny);
+      return;
+    }
+    for (int g = 0; g < G; ++g) {
+      if constexpr (PREC == 2) block_active_sums_df<kNT>(w.rho_df, w.xdfg(g), th, K, N, w.sumsg(g));
+      else block_active_sums<kNT, double>(w.rho, w.xg(g), th, K, N, w.sumsg(g));
+    }
+  }
+
+  // the off-grid sums by the non-uniform FFT (lse_nufft.cuh) rather than
+  // directly: for K frequencies at least cfg.nufft_min_k (0: never) and N >= 64
+  __device__ bool use_nufft(int K) const { return A->cfg.nufft_min_k > 0 && K >= A->cfg.nufft_min_k && N >= 64; }
+
+  __device__ void sums_nufft(const double* th, int K, c128* out, size_t stride) {
+    if constexpr (PREC == 2) {
+      block_sums_nufft<kNT>(PolDF{A->tab.twdf, A->tab.log2max}, w.rho_df, w.x_df, (size_t)w.ny, G, th, K, N,
+                            log2M2, w.nfac64, w.nfacdf, w.nu, out, stride);
+    } else {
+      block_sums_nufft<kNT>(Pol64{A->tab.tw64, A->tab.log2max}, (const float4*)w.rho, (const float4*)w.x,
+                            (size_t)w.ny, G, th, K, N, log2M2, w.nfac64, w.nfacdf, w.nu, out, stride);
+    }
   }
 
   // ---------------------------------------------------------------- grid ---
@@ -347,6 +408,17 @@ struct Fitter {
                        w.gbuf[1], w.gbuf[3], log2L, false, twg);
     block_fft<kNT, TG>([=] __device__(int i) { return i < n_ ? cvt<TG>(x[i]) : zero<TG>(); }, w.gbuf[2], w.gbuf[3],
                        log2L, false, twg);
+    if (G > 1) {  // Q = sum_g |q_g|^2 on the grid (Sec. V): one transform per snapshot
+      for (int l = threadIdx.x; l < L; l += kNT) w.gq2[l] = norm2(cvt<double>(w.gbuf[2][l]));
+      for (int g = 1; g < G; ++g) {
+        __syncthreads();
+        const c128* xv = w.xg(g);
+        block_fft<kNT, TG>([=] __device__(int i) { return i < n_ ? cvt<TG>(xv[i]) : zero<TG>(); }, w.gbuf[2],
+                           w.gbuf[3], log2L, false, twg);
+        for (int l = threadIdx.x; l < L; l += kNT) w.gq2[l] += norm2(cvt<double>(w.gbuf[2][l]));
+      }
+      __syncthreads();
+    }
     double gsum = 0.0;
     for (int k = threadIdx.x; k < K; k += kNT) gsum += w.gamma[k];
     gsum = block_sum<kNT>(gsum, sh->dred);
@@ -354,12 +426,12 @@ struct Fitter {
     const double lpo = log_prior_odds(sh->zeta);
     const double inv_delta = 1.0 / sh->delta_last;
     for (int l = threadIdx.x; l < L; l += kNT) {
-      const c128 Q0 = cvt<double>(w.gbuf[0][l]), Q1 = cvt<double>(w.gbuf[1][l]), q = cvt<double>(w.gbuf[2][l]);
+      const c128 Q0 = cvt<double>(w.gbuf[0][l]), Q1 = cvt<double>(w.gbuf[1][l]);
       const double s = 2.0 * inv_delta * (Q1 * conj(Q0)).re;
-      const double aq2 = norm2(q);
+      const double aq2 = G > 1 ? w.gq2[l] : norm2(cvt<double>(w.gbuf[2][l]));
       double gb = gbar;
-      if (K == 0) gb = aq2 > s ? (aq2 - s) / (s * s) : 0.0;
-      w.dl[l] = log1p(gb * s) + lpo - gb * aq2 / (1.0 + gb * s);
+      if (K == 0) gb = activate_gamma(aq2, s);
+      w.dl[l] = Gd * log1p(gb * s) + lpo - gb * aq2 / (1.0 + gb * s);
     }
     if (threadIdx.x == 0) {
       sh->gbar = gbar;
@@ -368,36 +440,60 @@ struct Fitter {
     __syncthreads();
   }
 
-  __device__ void grid_point(int l, double& s, c128& q) const {
+  // s and Q = sum_g |q_g|^2 at grid point l (after grid_delta)
+  __device__ void grid_point(int l, double& s, double& Q) const {
     const c128 Q0 = cvt<double>(w.gbuf[0][l]), Q1 = cvt<double>(w.gbuf[1][l]);
-    q = cvt<double>(w.gbuf[2][l]);
+    Q = G > 1 ? w.gq2[l] : norm2(cvt<double>(w.gbuf[2][l]));
     s = 2.0 / sh->delta_last * (Q1 * conj(Q0)).re;
   }
 
-  // Delta L of eq. (delta_L) from s and q at a grid point.
-  __device__ double delta_L(double s, c128 q, int K) const {
-    const double aq2 = norm2(q);
+  // gamma-hat of eq. (activate_gamma) from Q = sum_g |q_g|^2 and s: the
+  // minimiser of the single-component objective, (Q/G - s)/s^2 for G
+  // snapshots (Sec. V, eq. singlecomp-mmv)
+  __device__ double activate_gamma(double Q, double s) const {
+    const double Qg = Q / Gd;
+    return Qg > s ? (Qg - s) / (s * s) : 0.0;
+  }
+
+  // eq. (activate_criterion) (tau = 0: eq. activate_derived) in the mean
+  // per-snapshot form Q/(G s) > (1 + 1/(gb s)) (ln(1 + gb s) + ln((1-zeta)/zeta)/G) + tau
+  __device__ bool activation_test(double Q, double s, double gb, double tau) const {
+    const double gs = gb * s;
+    const double rhs = (1.0 + 1.0 / gs) * (log1p(gs) + sh->lpo / Gd) + tau;
+    return Q / Gd / s > rhs;
+  }
+
+  // Delta L of eq. (delta_L) (eq. singlecomp-mmv for G snapshots) from s and
+  // Q = sum_g |q_g|^2 at a grid point.
+  __device__ double delta_L(double s, double Q, int K) const {
     double gb = sh->gbar;
-    if (K == 0) gb = aq2 > s ? (aq2 - s) / (s * s) : 0.0;
-    return log1p(gb * s) + sh->lpo - gb * aq2 / (1.0 + gb * s);
+    if (K == 0) gb = activate_gamma(Q, s);
+    return Gd * log1p(gb * s) + sh->lpo - gb * Q / (1.0 + gb * s);
   }
 
   // FP64 re-evaluation of s, q and Delta L at grid points ls[0..n), n <=
   // kRescore, by the direct off-grid sums of Sec. III-B/C on the FP64
   // generators (mixed paths: the FP32 grid only proposes candidates).
-  __device__ void rescore(const int* ls, int n, double* dl_out, double* s_out, c128* q_out, int K) {
+  __device__ void rescore(const int* ls, int n, double* dl_out, double* s_out, double* Q_out, int K) {
     for (int j = threadIdx.x; j < n; j += kNT) w.rs_theta[j] = (double)ls[j] / (double)L;
     __syncthreads();
-    if constexpr (PREC == 2) block_active_sums_df<kNT>(w.rho_df, w.x_df, w.rs_theta, n, N, w.rs_sums);
-    else block_active_sums<kNT, double>(w.rho, w.x, w.rs_theta, n, N, w.rs_sums);
+    if (use_nufft(n)) {
+      sums_nufft(w.rs_theta, n, w.rs_sums, 7 * (size_t)kRescore);
+    } else {
+      for (int g = 0; g < G; ++g) {
+        if constexpr (PREC == 2) block_active_sums_df<kNT>(w.rho_df, w.xdfg(g), w.rs_theta, n, N, w.rssumsg(g));
+        else block_active_sums<kNT, double>(w.rho, w.xg(g), w.rs_theta, n, N, w.rssumsg(g));
+      }
+    }
     const double inv_delta = 1.0 / sh->delta_last;
     for (int j = threadIdx.x; j < n; j += kNT) {
       const c128* sm = w.rs_sums + 7 * j;
       const double sv = 2.0 * inv_delta * (sm[1] * conj(sm[0])).re;
-      const c128 qv = sm[4];
-      dl_out[j] = delta_L(sv, qv, K);
+      double Qv = norm2(sm[4]);
+      for (int g = 1; g < G; ++g) Qv += norm2(w.rssumsg(g)[7 * j + 4]);
+      dl_out[j] = delta_L(sv, Qv, K);
       s_out[j] = sv;
-      q_out[j] = qv;
+      Q_out[j] = Qv;
     }
     __syncthreads();
   }
@@ -427,7 +523,7 @@ struct Fitter {
       }
       __syncthreads();
     }
-    rescore(sh->top, sh->ntop, sh->top_dl, sh->top_s, sh->top_q, K);
+    rescore(sh->top, sh->ntop, sh->top_dl, sh->top_s, sh->top_Q, K);
   }
 
   // ---------------------------------------------------- exact activation ---
@@ -446,23 +542,22 @@ struct Fitter {
         for (int j = 0; j < sh->ntop; ++j) m = minloc(m, MinLoc{sh->top_dl[j], sh->top[j]});
       }
       if (threadIdx.x == 0) {
-        double s;
-        c128 q;
-        if constexpr (PREC == 0) {
-          grid_point(m.i, s, q);
+        double s = 0.0, Q = 0.0;
+        // no grid point compares below +inf (every Delta L NaN or +inf): nothing to activate
+        const bool found = m.i >= 0 && m.i < L;
+        if (!found) {
+        } else if constexpr (PREC == 0) {
+          grid_point(m.i, s, Q);
         } else {
           int jm = 0;
           for (int j = 0; j < sh->ntop; ++j)
             if (sh->top[j] == m.i) jm = j;
           s = sh->top_s[jm];
-          q = sh->top_q[jm];
+          Q = sh->top_Q[jm];
         }
-        const double aq2 = norm2(q);
-        const double ghat = aq2 > s ? (aq2 - s) / (s * s) : 0.0;
+        const double ghat = found ? activate_gamma(Q, s) : 0.0;
         const double gb = K ? sh->gbar : ghat;
-        const double gs = gb * s;
-        const double rhs = (1.0 + 1.0 / gs) * (log1p(gs) + sh->lpo) + sh->tau;
-        const bool ok = ghat > 0.0 && m.v < -kEpsL && aq2 / s > rhs;
+        const bool ok = found && ghat > 0.0 && m.v < -kEpsL && activation_test(Q, s, gb, sh->tau);
         sh->flag = ok;
         if (ok) {
           w.theta[K] = (double)m.i / (double)L;
@@ -522,17 +617,16 @@ struct Fitter {
     if constexpr (PREC == 0) {
       for (int j = threadIdx.x; j < nc; j += kNT) {
         const int l = w.cand[j];
-        double sv;
-        c128 qv;
-        grid_point(l, sv, qv);
+        double sv, Qv;
+        grid_point(l, sv, Qv);
         w.cand_dl[j] = w.dl[l];
         w.cand_s[j] = sv;
-        w.cand_q[j] = qv;
+        w.cand_Q[j] = Qv;
       }
       __syncthreads();
     } else {
       for (int j0 = 0; j0 < nc; j0 += kRescore)
-        rescore(w.cand + j0, min(kRescore, nc - j0), w.cand_dl + j0, w.cand_s + j0, w.cand_q + j0, K0);
+        rescore(w.cand + j0, min(kRescore, nc - j0), w.cand_dl + j0, w.cand_s + j0, w.cand_Q + j0, K0);
     }
     int n_act = 0;
     const double min_sep = 0.05 / (double)N;
@@ -561,13 +655,10 @@ struct Fitter {
       close = __syncthreads_or(close);
       if (threadIdx.x == 0 && !close && sh->K < N) {
         const double s = w.cand_s[sh->sel];
-        const c128 q = w.cand_q[sh->sel];
-        const double aq2 = norm2(q);
-        const double ghat = aq2 > s ? (aq2 - s) / (s * s) : 0.0;
+        const double Q = w.cand_Q[sh->sel];
+        const double ghat = activate_gamma(Q, s);
         const double gb = K0 ? sh->gbar : ghat;
-        const double gs = gb * s;
-        const double rhs = (1.0 + 1.0 / gs) * (log1p(gs) + sh->lpo);
-        if (ghat > 0.0 && aq2 / s > rhs) {
+        if (ghat > 0.0 && activation_test(Q, s, gb, 0.0)) {
           w.theta[sh->K] = th;
           w.gamma[sh->K] = ghat;
           sh->K = sh->K + 1;
@@ -595,8 +686,14 @@ struct Fitter {
     double dec = 0.0, slope = 0.0, amax = HUGE_VAL;
     for (int k = threadIdx.x; k < K; k += kNT) {
       const double g = w.gamma[k];
-      const CompVec cv = component_vectors<double>(w.sums + 7 * k, inv_delta);
-      const Derivs d = objective_derivatives(cv, g);
+      Derivs d = objective_derivatives(component_vectors<double>(w.sums + 7 * k, inv_delta), g);
+      for (int gi = 1; gi < G; ++gi) {  // Sec. V: the derivatives sum over snapshots
+        const Derivs e = objective_derivatives(component_vectors<double>(w.sumsg(gi) + 7 * k, inv_delta), g);
+        d.gt += e.gt;
+        d.gg += e.gg;
+        d.ht += e.ht;
+        d.hg += e.hg;
+      }
       const double ht = d.ht > 0.0 ? d.ht : h_theta_fb;
       const double hg = d.hg > 0.0 ? d.hg : 1.0 / (g * g);
       const double dt = -d.gt / ht, dg = -d.gg / hg;
@@ -610,7 +707,7 @@ struct Fitter {
     slope = block_sum<kNT>(slope, sh->dred);
     MinLoc am{amax, 0};
     am = block_minloc<kNT>(am, sh->ml);
-    if (dec < N * 1e-8) return dec;
+    if (dec < (double)(G * N) * 1e-8) return dec;
     double alpha = am.v < HUGE_VAL ? fmin(1.0, 0.99 * am.v) : 1.0;
     const double f0 = sh->f_cur;
     for (int j = 0; j < 31; ++j) {
@@ -651,8 +748,10 @@ struct Fitter {
         const CompVec cv = component_vectors<double>(w.sums + 7 * k, inv_delta);
         const double den = 1.0 - g * cv.s;
         const double st = cv.s / den;
-        const double aq2 = norm2(cv.q) / (den * den);
-        const double stat = g * aq2 / (1.0 + g * st) - log1p(g * st);
+        double qq = norm2(cv.q);
+        for (int gi = 1; gi < G; ++gi) qq += norm2(w.sumsg(gi)[7 * k + 4]);
+        const double aq2 = qq / (den * den);
+        const double stat = g * aq2 / (1.0 + g * st) - Gd * log1p(g * st);
         if (stat < thr) m = minloc(m, MinLoc{stat, k});
       }
       m = block_minloc<kNT>(m, sh->ml);
@@ -688,12 +787,17 @@ struct Fitter {
     L = d.L;
     log2L = ilog2((uint32_t)L);
     log2M2 = ilog2(2u * (uint32_t)N);
-    const float* yin = A->y + 2 * d.y_off;
+    G = A->cfg.G;
+    Gd = (double)G;
     double part = 0.0;
-    for (int n = threadIdx.x; n < N; n += kNT) {
-      const c128 v = mk((double)yin[2 * n], (double)yin[2 * n + 1]);
-      w.y[n] = v;
-      part += norm2(v);
+    for (int g = 0; g < G; ++g) {  // snapshot g of instance b at G y_off + g N (complex elements)
+      const float* yin = A->y + 2 * ((int64_t)G * d.y_off + (int64_t)g * N);
+      c128* yv = w.yg(g);
+      for (int n = threadIdx.x; n < N; n += kNT) {
+        const c128 v = mk((double)yin[2 * n], (double)yin[2 * n + 1]);
+        yv[n] = v;
+        part += norm2(v);
+      }
     }
     const double yy = block_sum<kNT>(part, sh->dred);
     // Levinson arrays in shared memory when they fit and the Levinson
@@ -723,8 +827,8 @@ struct Fitter {
       sh->status = kST_OK;
       sh->n_evals = 0;
       sh->n_grid = 0;
-      sh->beta = 0.01 * yy / N;
-      sh->eps_beta = 1e-12 * yy / N;
+      sh->beta = 0.01 * yy / (double)(G * N);
+      sh->eps_beta = 1e-12 * yy / (double)(G * N);
       sh->zeta = 0.2;
       sh->tau = A->cfg.tau;
     }
@@ -739,10 +843,13 @@ struct Fitter {
       __syncthreads();
       return;
     }
-    const c128* yv = w.y;
+    if (A->cfg.nufft_min_k > 0 && N >= 64) nufft_factors<kNT>(N, 1 << log2M2, w.nfac64, w.nfacdf);
     const int n_ = N;
-    block_fft<kNT, double>([=] __device__(int i) { return i < n_ ? yv[i] : zero<double>(); }, w.Yf, w.buf[4], log2M2,
-                           false, tw64);
+    for (int g = 0; g < G; ++g) {
+      const c128* yv = w.yg(g);
+      block_fft<kNT, double>([=] __device__(int i) { return i < n_ ? yv[i] : zero<double>(); }, w.Yfg(g), w.buf[4],
+                             log2M2, false, tw64);
+    }
     int st = evaluate(w.theta, w.gamma, 0, true);
     double L_prev = sh->f_cur - prior_term(0, N, sh->zeta);
     bool approx = A->cfg.approx_iters > 0;
@@ -776,13 +883,17 @@ struct Fitter {
           const c128 r1r0 = sm[1] * conj(sm[0]);
           sg += 2.0 * r1r0.re * inv_delta * w.gamma[k];
         }
-        for (int n = threadIdx.x; n < N; n += kNT) xx += norm2(w.x[n]);
+        for (int g = 0; g < G; ++g) {
+          const c128* xv = w.xg(g);
+          for (int n = threadIdx.x; n < N; n += kNT) xx += norm2(xv[n]);
+        }
         sg = block_sum<kNT>(sg, sh->dred);
         xx = block_sum<kNT>(xx, sh->dred);
         if (threadIdx.x == 0) {
           sh->zeta = fmin(0.5, (double)K / (double)N);
           const double b0 = sh->beta;
-          sh->beta = fmax(sh->eps_beta, (b0 * sg + b0 * b0 * xx) / N);
+          // Sec. V: the residual term is the mean over snapshots
+          sh->beta = fmax(sh->eps_beta, (b0 * sg + b0 * b0 * (xx / Gd)) / N);
         }
         __syncthreads();
         if (evaluate(w.theta, w.gamma, K, true)) {
@@ -796,11 +907,11 @@ struct Fitter {
         if (sh->K == 0) break;
         const double dec = newton_iteration();
         deactivation();
-        if (dec < N * 1e-8) break;
+        if (dec < (double)(G * N) * 1e-8) break;
       }
       if (sh->status != kST_OK) break;
       const double L_cur = sh->f_cur - prior_term(sh->K, N, sh->zeta);
-      if (fabs(L_cur - L_prev) < N * 1e-7) {
+      if (fabs(L_cur - L_prev) < (double)(G * N) * 1e-7) {
         converged = true;
         break;
       }
@@ -818,10 +929,10 @@ struct Fitter {
         r += (u < t) || (u == t && j < k);
       }
       const double g = w.gamma[k];
-      const c128 q = w.sums[7 * k + 4];
       o.theta[ro + r] = t;
       o.gamma[ro + r] = g;
-      o.alpha[ro + r] = g * q;
+      for (int gi = 0; gi < G; ++gi)  // alpha^(g) = gamma q_g at G ro + g N (eq. bmu, Sec. V)
+        o.alpha[(int64_t)G * ro + (int64_t)gi * N + r] = g * w.sumsg(gi)[7 * k + 4];
     }
     if (threadIdx.x == 0) {
       o.K[ob] = K;
@@ -880,7 +991,7 @@ __global__ void __launch_bounds__(threads_for<PREC>(), 1) fit_kernel(FitArgs arg
   F.sh = &sh;
   F.dsm = dsm;
   F.A = &args;
-  F.w = carve<TG>(args.ws + (size_t)unit * args.ws_bytes, args.Nmax, args.Lmax);
+  F.w = carve<TG>(args.ws + (size_t)unit * args.ws_bytes, args.Nmax, args.Lmax, args.cfg.G);
   F.tw64 = Twiddles<double>{args.tab.tw64, args.tab.log2max};
   if constexpr (PREC != 0) F.twg = Twiddles<TG>{(const cx<TG>*)args.tab.tw32, args.tab.log2max};
   else F.twg = Twiddles<TG>{(const cx<TG>*)args.tab.tw64, args.tab.log2max};
@@ -903,9 +1014,10 @@ __global__ void __launch_bounds__(threads_for<PREC>(), 1) fit_kernel(FitArgs arg
 }  // namespace
 
 int superfast_min_n(uint64_t flags) { return (flags & LSE_FLAG_LEVINSON) ? 0 : kSuperfastMinN; }
+int nufft_min_k(uint64_t flags) { return (flags & LSE_FLAG_DIRECT_SUMS) ? 0 : kNufftMinK; }
 
-size_t fit_workspace_bytes(int Nmax, int Lmax, int prec) {
-  return prec ? make_layout<float>(Nmax, Lmax).total : make_layout<double>(Nmax, Lmax).total;
+size_t fit_workspace_bytes(int Nmax, int Lmax, int prec, int G) {
+  return prec ? make_layout<float>(Nmax, Lmax, G).total : make_layout<double>(Nmax, Lmax, G).total;
 }
 int fit_smem_bytes() { return kSmemBytes; }
 
@@ -945,7 +1057,7 @@ cudaError_t launch_fit(int prec, const float* y, const InstDesc* inst, int B, in
   a.tab = tab;
   a.out = out;
   a.ws = (char*)ws;
-  a.ws_bytes = fit_workspace_bytes(Nmax, Lmax, prec);
+  a.ws_bytes = fit_workspace_bytes(Nmax, Lmax, prec, cfg.G);
   a.counter = counter;
   // Clusters (double-float path): of two blocks, sharing every recursion
   // through shared memory, when the batch leaves a spare SM per instance and

@@ -6,11 +6,16 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/lse.h"
 #include "lse_common.cuh"
 
 struct lse_ctx;
 // the stream a context enqueues on (lse_api.cu)
 cudaStream_t lse_ctx_stream(lse_ctx* c);
+// grow a context's device memory (fit workspace, twiddle tables, launch
+// descriptors and their pinned staging) for fits of B instances up to
+// (Nmax, Lmax), so that such fits allocate nothing; waits for the device
+lse_status lse_ctx_reserve_fit(lse_ctx* c, int Nmax, int Lmax, int B);
 
 namespace lse {
 
@@ -31,7 +36,12 @@ struct FitConfig {
   int cluster;    // thread-block clusters allowed for the Levinson recursion (double-float path)
   int sf_min_n;   // instances with N >= sf_min_n use the superfast Schur recursion (0: none)
   int Nmin;       // smallest N of the launch
+  int G = 1;      // snapshots per instance (multiple measurement vectors, Sec. V)
+  int nufft_min_k = 0;  // off-grid sums at >= this many frequencies by the non-uniform FFT (0: never)
 };
+
+// nufft_min_k for the lse_config flags (LSE_FLAG_DIRECT_SUMS: 0)
+int nufft_min_k(uint64_t flags);
 
 // Smallest N for which the superfast Schur recursion replaces the Levinson
 // recursion, given the lse_config flags (LSE_FLAG_LEVINSON: never).
@@ -60,8 +70,9 @@ struct Tables {
   const float4* twdf;
 };
 
-// Per-CTA workspace needed by the fit kernel for instances up to (Nmax, Lmax).
-size_t fit_workspace_bytes(int Nmax, int Lmax, int prec);
+// Per-CTA workspace needed by the fit kernel for instances up to (Nmax, Lmax)
+// with G snapshots each.
+size_t fit_workspace_bytes(int Nmax, int Lmax, int prec, int G = 1);
 int fit_smem_bytes();
 
 // Launch the persistent fit kernel over B instances on `stream` with `grid`

@@ -312,6 +312,22 @@ int32_t lse_serve_in_flight(const lse_server* s) {
 
 uint64_t lse_serve_device_bytes(const lse_server* s) { return s ? s->in_use : 0; }
 
+lse_status lse_serve_reserve(lse_server* s, int32_t n_max) {
+  if (!s || n_max < 2 || n_max > (1 << 17)) return LSE_EINVAL;
+  const int L = s->cfg.grid_size ? s->cfg.grid_size : default_L(n_max);
+  if (L < 2 * n_max) return LSE_EINVAL;
+  for (Slot& sl : s->slots) {
+    if (sl.busy) {  // its group must finish before its buffers can change
+      cudaEventSynchronize(sl.done);
+      harvest(s, sl);
+    }
+    lse_status st = grow_slot(sl, (size_t)s->max_group * (size_t)n_max, (size_t)s->max_group);
+    if (st) return st;
+    if ((st = lse_ctx_reserve_fit(sl.ctx, n_max, L, s->max_group))) return st;
+  }
+  return LSE_OK;
+}
+
 void lse_serve_destroy(lse_server* s) {
   if (!s) return;
   for (Slot& sl : s->slots) {

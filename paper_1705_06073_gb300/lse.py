@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(HERE, "_build", "liblse.so")
 LSE_OK, LSE_EINVAL, LSE_ENOMEM, LSE_EBUDGET, LSE_ENUMERIC, LSE_ENOTCONV, LSE_ETIMEOUT, LSE_ECUDA, LSE_ECAPACITY = range(9)
 LSE_PREC_FP64, LSE_PREC_MIXED, LSE_PREC_MIXED_DF = 0, 1, 2
 LSE_F32, LSE_F64 = 0, 1
-LSE_FLAG_NO_AUTOTUNE, LSE_FLAG_NO_CLUSTER, LSE_FLAG_LEVINSON = 1, 2, 4
+LSE_FLAG_NO_AUTOTUNE, LSE_FLAG_NO_CLUSTER, LSE_FLAG_LEVINSON, LSE_FLAG_DIRECT_SUMS = 1, 2, 4, 8
 
 c_double_p = ctypes.POINTER(ctypes.c_double)
 c_int32_p = ctypes.POINTER(ctypes.c_int32)
@@ -60,7 +60,8 @@ class lse_batch_out(ctypes.Structure):
 EXPORTS = ["lse_config_default", "lse_create", "lse_destroy", "lse_strerror", "lse_last_error", "lse_fit",
            "lse_fit_batch", "lse_fit_batch_d", "lse_eval_grid", "lse_eval_grid_batch_d", "lse_kernel_time",
            "lse_plan_fit", "lse_plan_launch", "lse_plan_graph_launch", "lse_plan_destroy", "lse_serve_create",
-           "lse_serve_submit", "lse_serve_poll", "lse_serve_in_flight", "lse_serve_device_bytes", "lse_serve_destroy"]
+           "lse_serve_submit", "lse_serve_poll", "lse_serve_in_flight", "lse_serve_device_bytes", "lse_serve_destroy",
+           "lse_fit_mmv", "lse_fit_mmv_batch_d", "lse_serve_reserve"]
 
 _lib = None
 
@@ -84,6 +85,9 @@ def load(path: str = LIB_PATH):
         "lse_fit_batch": (ctypes.c_int, [P, c_float_p, c_int64_p, ctypes.c_int32, ctypes.POINTER(lse_result),
                                          c_int32_p]),
         "lse_fit_batch_d": (ctypes.c_int, [P, P, c_int64_p, ctypes.c_int32, ctypes.POINTER(lse_batch_out), P]),
+        "lse_fit_mmv": (ctypes.c_int, [P, c_float_p, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(lse_result)]),
+        "lse_fit_mmv_batch_d": (ctypes.c_int, [P, P, c_int64_p, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.POINTER(lse_batch_out), P]),
         "lse_eval_grid": (ctypes.c_int, [P, c_float_p, ctypes.c_int32, c_double_p, c_double_p, ctypes.c_int32,
                                          ctypes.c_double, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, P]),
         "lse_eval_grid_batch_d": (ctypes.c_int, [P, P, c_int64_p, ctypes.c_int32, P, P, c_int64_p, P, c_int32_p,
@@ -100,6 +104,7 @@ def load(path: str = LIB_PATH):
         "lse_serve_in_flight": (ctypes.c_int32, [P]),
         "lse_serve_device_bytes": (ctypes.c_uint64, [P]),
         "lse_serve_destroy": (None, [P]),
+        "lse_serve_reserve": (ctypes.c_int, [P, ctypes.c_int32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -214,6 +219,44 @@ def lse_fit_batch_d(ctx, y_d, offsets: np.ndarray, out: dict, stream=None) -> No
     _check(ctx, st)
 
 
+def lse_fit_mmv(ctx, Y, K_cap: int | None = None) -> dict:
+    """Fit one instance of G snapshots (Sec. V): Y a G x N complex array
+    (snapshot g = Y[g]); returns dict(theta, gamma, alpha [K x G], beta, ...)."""
+    Y = np.ascontiguousarray(np.asarray(Y, dtype=np.complex64))
+    if Y.ndim == 1:
+        Y = Y[None, :]
+    G, N = Y.shape
+    cap = N if K_cap is None else K_cap
+    th = np.zeros(cap)
+    ga = np.zeros(cap)
+    al = np.zeros(2 * cap * G)
+    r = lse_result()
+    r.K_cap = cap
+    r.theta = _ptr(th, c_double_p)
+    r.gamma = _ptr(ga, c_double_p)
+    r.alpha = _ptr(al, c_double_p)
+    st = load().lse_fit_mmv(ctx, Y.view(np.float32).ctypes.data_as(c_float_p), N, G, ctypes.byref(r))
+    if st not in (LSE_OK, LSE_ENOTCONV):
+        _check(ctx, st)
+    K = r.K
+    a = (al[0::2] + 1j * al[1::2]).reshape(G, cap)[:, :K].T.copy()
+    return dict(K=K, theta=th[:K].copy(), gamma=ga[:K].copy(), alpha=a, beta=r.beta, objective=r.objective,
+                iters=r.iters, n_evals=r.n_evals, n_grid=r.n_grid, status=int(st))
+
+
+def lse_fit_mmv_batch_d(ctx, y_d, offsets: np.ndarray, G: int, out: dict, stream=None) -> None:
+    """Device batched fit of instances of G snapshots: y_d a torch complex64
+    CUDA tensor (instance b's snapshot g at G offsets[b] + g N_b), offsets a
+    host int64 array [B+1] of samples per snapshot, out as from
+    alloc_batch_out(offsets, G=G)."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    bo = _batch_out(out)
+    s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    st = load().lse_fit_mmv_batch_d(ctx, ctypes.c_void_p(y_d.data_ptr()), _ptr(offsets, c_int64_p),
+                                    len(offsets) - 1, int(G), ctypes.byref(bo), s)
+    _check(ctx, st)
+
+
 def _batch_out(out: dict):
     return lse_batch_out(out["theta"].data_ptr(), out["gamma"].data_ptr(), out["alpha"].data_ptr(),
                          out["K"].data_ptr(), out["beta"].data_ptr(), out["objective"].data_ptr(),
@@ -242,14 +285,14 @@ def lse_plan_destroy(plan) -> None:
     load().lse_plan_destroy(plan)
 
 
-def alloc_batch_out(offsets: np.ndarray, device="cuda"):
+def alloc_batch_out(offsets: np.ndarray, device="cuda", G: int = 1):
     import torch
     tot = int(offsets[-1])
     B = len(offsets) - 1
     f64 = dict(dtype=torch.float64, device=device)
     i32 = dict(dtype=torch.int32, device=device)
     return dict(theta=torch.zeros(tot, **f64), gamma=torch.zeros(tot, **f64),
-                alpha=torch.zeros(tot, dtype=torch.complex128, device=device), K=torch.zeros(B, **i32),
+                alpha=torch.zeros(G * tot, dtype=torch.complex128, device=device), K=torch.zeros(B, **i32),
                 beta=torch.zeros(B, **f64), objective=torch.zeros(B, **f64), iters=torch.zeros(B, **i32),
                 n_evals=torch.zeros(B, **i32), n_grid=torch.zeros(B, **i32), status=torch.zeros(B, **i32))
 
@@ -360,6 +403,10 @@ class Server:
                 self._buf[i].K_cap = self.K_cap
             if n < 64:
                 return out
+
+    def reserve(self, n_max: int) -> None:
+        """Grow every slot for a full group of requests of up to n_max samples."""
+        _check(None, load().lse_serve_reserve(self.h, int(n_max)))
 
     def in_flight(self) -> int:
         return load().lse_serve_in_flight(self.h)

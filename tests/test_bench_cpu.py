@@ -27,9 +27,17 @@ def test_reference_arm_prints_the_contract_line():
 def test_roofline_bookkeeping():
     sys.path.insert(0, ROOT)
     import bench
-    # 252 FP32 flops per (i, n-i) pair, n^2/4 pairs
-    assert bench.levinson_df_flops(4096) == 252.0 * 4096 * 4096 / 4
     assert bench.levinson_flops(100) == 8.0 * 100 * 100
+    assert bench.fft_flops(1024) == 5.0 * 1024 * 10
+    assert bench.pow2_at_least(1000) == 1024 and bench.pow2_at_least(1024) == 1024
+    # a leaf-sized factorisation: one leaf of n - 1 <= 32 orders plus the refinement FFTs
+    assert bench.schur_flops(33) == 8.0 * 4 * 32 * 32 + 9 * bench.fft_flops(128)
+    # the superfast count grows like n log^2 n: far below the Levinson count at large n
+    assert bench.schur_flops(65536) < 0.05 * bench.levinson_flops(65536)
+    assert bench.schur_flops(1 << 14) / bench.schur_flops(1 << 13) < 2.5
+    # direct sums below 32 frequencies, the non-uniform FFT from 32 on
+    n = 4096
+    assert bench.eval_flops(n, 31) - bench.eval_flops(n, 0) == 8.0 * n * 31 + 7 * 8.0 * n * 31
     # the traffic figure is reported only for the sources it was measured on
     d = bench.sources_digest()
     assert len(d) == 64
