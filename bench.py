@@ -109,25 +109,34 @@ def levinson_flops(n: int) -> float:
     return 8.0 * n * n
 
 
-# DRAM traffic of fit_kernel<2> (dram__bytes_read.sum + dram__bytes_write.sum,
-# one ncu capture of the 8-instance case of this workload, divided by 8) and
-# the digest of the CUDA sources it was taken on; reported only while the
-# sources are unchanged.
-FIT_TRAFFIC = {"sources_sha256": "212404002da74e5f3a8b2bd4e0dcef329a33624762a89115a2a4b93d982f4a60",
-               "bytes_per_instance": (4016896 + 1272320) / 8}
+# Sources each kernel is compiled from (its translation unit and the device
+# headers it includes); a traffic figure below is reported only while they
+# hash to the digest it was measured on.
+FIT_SOURCES = ["lse_fit.cu", "lse_common.cuh", "lse_device.cuh", "lse_df64.cuh", "lse_nufft.cuh", "lse_schur.cuh"]
+GRID_SOURCES = ["lse_grid.cu", "lse_common.cuh", "lse_device.cuh", "lse_df64.cuh", "lse_fft_smem.cuh", "lse_schur.cuh"]
+
+# DRAM traffic of fit_kernel<2> per instance in the 64-instance launch
+# (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of this
+# workload, divided by 64: the per-block workspaces, ~10 MB each, do not fit
+# the L2 together, so intermediate FFT buffers are written back).
+FIT_TRAFFIC = {"sources_sha256": "8ab823405b4caa6fb74f04214bdd1202d42dd72137c456ea5f2cd24935d7cf7a",
+               "bytes_per_instance": (1564979712 + 11565479424) / 64}
 
 
-def sources_digest() -> str:
-    """sha256 over the CUDA sources and the public header, in name order, with
-    comments and blank lines removed (a comment edit does not change the
-    kernels the traffic was measured on)."""
+def sources_digest(files=None) -> str:
+    """sha256 over the given CUDA sources (default: all of them and the public
+    header), in name order, with comments and blank lines removed (a comment
+    edit does not change the kernels a figure was measured on)."""
     import hashlib
     import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1705_06073_gb300", "csrc")
-    files = sorted(os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith((".cu", ".cuh", ".h")))
-    files.append(os.path.join(ROOT, "include", "lse.h"))
-    for f in files:
+    if files is None:
+        paths = sorted(os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith((".cu", ".cuh", ".h")))
+        paths.append(os.path.join(ROOT, "include", "lse.h"))
+    else:
+        paths = [os.path.join(csrc, f) for f in sorted(files)]
+    for f in paths:
         with open(f, encoding="utf-8") as fh:
             text = fh.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
@@ -139,7 +148,7 @@ def sources_digest() -> str:
 
 
 def fit_traffic(b: int):
-    if FIT_TRAFFIC["bytes_per_instance"] is None or FIT_TRAFFIC["sources_sha256"] != sources_digest():
+    if FIT_TRAFFIC["bytes_per_instance"] is None or FIT_TRAFFIC["sources_sha256"] != sources_digest(FIT_SOURCES):
         return None
     return FIT_TRAFFIC["bytes_per_instance"] * b
 
@@ -158,13 +167,15 @@ def hbm_peak():
 
 
 # DRAM traffic of grid_fft_kernel<float> per instance of the N = 4096,
-# L = 16384 batch (ncu dram__bytes_read.sum + dram__bytes_write.sum), with the
-# digest of the sources it was taken on; reported only while they match.
-GRID_TRAFFIC = {"sources_sha256": None, "bytes_per_instance": None}
+# L = 16384 batch (ncu dram__bytes_read.sum + dram__bytes_write.sum of the
+# timed launches, divided by 64): the inputs are read once; the 42 MB of
+# outputs stay in the L2 when the kernel ends, so no write reaches DRAM
+# within it.
+GRID_TRAFFIC = {"sources_sha256": "325621b06ed572d58432265628e68c38e2a8874376251e3bdb87e04e742e951a", "bytes_per_instance": 6407936 / 64}
 
 
 def grid_traffic(b: int):
-    if GRID_TRAFFIC["bytes_per_instance"] is None or GRID_TRAFFIC["sources_sha256"] != sources_digest():
+    if GRID_TRAFFIC["bytes_per_instance"] is None or GRID_TRAFFIC["sources_sha256"] != sources_digest(GRID_SOURCES):
         return None
     return GRID_TRAFFIC["bytes_per_instance"] * b
 
