@@ -6,19 +6,23 @@ superfast evaluations of Sec. III) of a batch of 64 synthetic instances with
 N = 4096 complex64 samples, K = 64 sinusoids (separation 2/N, alpha ~
 CN(0,1)), SNR uniform on [10, 30] dB per instance and an L = 4N = 16384
 point grid, in one launch of the persistent fit kernel.  The headline path
-is LSE_PREC_MIXED_DF: the first column, the generator recursion, the
-Gohberg-Semencul transforms and the off-grid Newton sums in double-float
+is LSE_PREC_MIXED_DF: the first column, the superfast Schur recursion for
+the Gohberg-Semencul generator, the Gohberg-Semencul transforms and the
+off-grid Newton sums (a non-uniform FFT at K >= 32) in double-float
 arithmetic on the FP32 pipes, the objective and the beta/gamma updates in
 FP64, the grid spectra in FP32 with every grid decision re-scored at the
 higher precision.  The plain FP64 path and the FP64-recursion mixed path are
 timed on the same batch beside it.  Grid-point throughput (first column,
-recursion, Gohberg-Semencul apply and all six grid outputs, Sec. III-D) is
-measured on the same batch at the fitted states, and on the single
-N = 65536, L = 131072 instance at its true state.
+factorisation, Gohberg-Semencul apply and all six grid outputs, Sec. III-D)
+is measured on the same batch at the fitted states, and on the single
+N = 65536, L = 131072 instance at its true state.  Further legs: the ragged
+1024-instance batch as one CUDA-graph launch, multiple measurement vectors
+(Sec. V), incomplete observations (the semifast evaluation and fits of
+Sec. IV), and continuous-batching serving over two 60 s Poisson windows.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank fits its own batch (weak scaling, no data-path
-collective); rank 0 prints one JSON line.
+collective); rank 0 prints one JSON line.  Progress lines go to stderr.
 """
 from __future__ import annotations
 
@@ -580,6 +584,115 @@ def mmv_leg(lse, dev, steps, warmup, flush):
             "headline_over_fp64": res["mixed_df"]["value"] / res["fp64"]["value"]}
 
 
+def semifast_flops(n: int, m: int, k: int, l: int) -> float:
+    """Algorithmic flops of one semifast evaluation with its grid (Sec. IV):
+    6 non-uniform-FFT transforms of M2 = pow2 >= 2n and their 16-tap
+    interpolations at the k^2 differences (3 sequences) and k frequencies (3),
+    the FFT of y on the grid, the grid's k x l matrix by 16-tap
+    interpolation, the forward substitution per grid point (k^2/2 complex
+    multiply-adds) and the k x k algebra (Cholesky k^3/6, three triangular
+    solves k^3/2 each); 8 flops per complex multiply-add."""
+    m2 = pow2_at_least(2 * n)
+    cm = 8.0
+    return (6 * fft_flops(m2) + cm * 16 * (3 * k * k + 3 * k) + fft_flops(l) + cm * 16 * k * l
+            + cm * l * k * k / 2 + cm * (k ** 3 / 6 + 3 * k ** 3 / 2 + 3 * k * k))
+
+
+def semifast_leg(lse, dev, steps, warmup, flush):
+    """Incomplete observations (Sec. IV): 64 instances observed at M = 3072 of
+    N = 4096 samples, K = 16, 20 dB, L = 4N; one semifast evaluation with the
+    grid q and s per instance per step, at the true states, and whole fits of
+    the batch (lse_fit_incomplete_batch_d, L = 8N by default); the headline
+    (double-float) and plain FP64 paths."""
+    import numpy as _np
+    import torch as _torch
+    from paper_1705_06073_gb300 import synth
+    work = synth.incomplete_batch()
+    B = len(work)
+    moff = _np.concatenate([[0], _np.cumsum([len(m.y) for m, _ in work])]).astype(_np.int64)
+    koff = _np.concatenate([[0], _np.cumsum([len(m.theta) for m, _ in work])]).astype(_np.int64)
+    Ns = _np.array([m.N for m, _ in work], _np.int32)
+    Ls = _np.array([L for _, L in work], _np.int32)
+    y = _torch.from_numpy(_np.concatenate([m.y for m, _ in work])).to(dev)
+    obs = _torch.from_numpy(_np.concatenate([m.obs for m, _ in work]).astype(_np.int32)).to(dev)
+    th = _torch.from_numpy(_np.concatenate([m.theta for m, _ in work])).to(dev)
+    ga = _torch.from_numpy(_np.concatenate([_np.abs(m.alpha) ** 2 for m, _ in work])).to(dev)
+    be = _torch.tensor([m.beta for m, _ in work], dtype=_torch.float64, device=dev)
+    st = _torch.cuda.Stream(device=dev)
+    res = {}
+    G = int(Ls.sum())
+    flops = sum(semifast_flops(m.N, len(m.y), len(m.theta), L) for m, L in work)
+    for name, prec in (("mixed_df", lse.LSE_PREC_MIXED_DF), ("fp64", lse.LSE_PREC_FP64)):
+        f64 = name == "fp64"
+        scal = _torch.zeros(2 * B, dtype=_torch.float64, device=dev)
+        vec = _torch.zeros(7 * int(koff[-1]), dtype=_torch.complex128, device=dev)
+        status = _torch.zeros(B, dtype=_torch.int32, device=dev)
+        q = _torch.zeros(G, dtype=_torch.complex128 if f64 else _torch.complex64, device=dev)
+        sg = _torch.zeros(G, dtype=_torch.float64 if f64 else _torch.float32, device=dev)
+        ctx = lse.lse_create(lse.lse_config_default(device=dev.index or 0, precision=prec))
+        try:
+            for _ in range(warmup):
+                lse.lse_eval_semifast_batch_d(ctx, y, obs, moff, Ns, th, ga, koff, be, Ls, scal, vec, status, q=q,
+                                              s=sg, f64=f64, stream=st)
+            st.synchronize()
+            lse.lse_kernel_time(ctx, 1)
+            ms = []
+            for _ in range(steps):
+                with _torch.cuda.stream(st):
+                    flush.zero_()
+                    e0 = _torch.cuda.Event(enable_timing=True)
+                    e1 = _torch.cuda.Event(enable_timing=True)
+                    e0.record(st)
+                    lse.lse_eval_semifast_batch_d(ctx, y, obs, moff, Ns, th, ga, koff, be, Ls, scal, vec, status,
+                                                  q=q, s=sg, f64=f64, stream=st)
+                    e1.record(st)
+                st.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            kms, kl = lse.lse_kernel_time(ctx, 1)
+            k_ms = kms / max(kl, 1)
+            res[name] = {"evaluations_per_s": B * steps / (sum(ms) / 1e3), "ms_per_batch": sum(ms) / steps,
+                         "grid_pt_evals_per_s": G * steps / (sum(ms) / 1e3), "kernel_ms": k_ms,
+                         "achieved_tflops": flops / (k_ms / 1e3) / 1e12,
+                         "status_nonzero": int(_torch.count_nonzero(status).item())}
+        finally:
+            lse.lse_destroy(ctx)
+    # the estimator on the same batch, every evaluation semifast
+    fits = {}
+    for name, prec in (("mixed_df", lse.LSE_PREC_MIXED_DF), ("fp64", lse.LSE_PREC_FP64)):
+        ctx = lse.lse_create(lse.lse_config_default(device=dev.index or 0, precision=prec))
+        try:
+            out = lse.alloc_batch_out(moff, device=dev)
+            for _ in range(max(1, warmup)):
+                lse.lse_fit_incomplete_batch_d(ctx, y, obs, moff, Ns, out, st)
+            st.synchronize()
+            ms = []
+            for _ in range(steps):
+                with _torch.cuda.stream(st):
+                    flush.zero_()
+                    e0 = _torch.cuda.Event(enable_timing=True)
+                    e1 = _torch.cuda.Event(enable_timing=True)
+                    e0.record(st)
+                    lse.lse_fit_incomplete_batch_d(ctx, y, obs, moff, Ns, out, st)
+                    e1.record(st)
+                st.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            Kf = out["K"].cpu().numpy()
+            fits[name] = {"fitted_instances_per_s": B * steps / (sum(ms) / 1e3), "ms_per_step": sum(ms) / steps,
+                          "K_mean": float(Kf.mean()), "n_evals_mean": float(out["n_evals"].float().mean().item()),
+                          "status_nonzero": int(_torch.count_nonzero((out["status"] != 0) & (out["status"] != 5)).item())}
+        finally:
+            lse.lse_destroy(ctx)
+    peak = {"mixed_df": FP32_PEAK_TFLOPS, "fp64": FP64_PEAK_TFLOPS}
+    for name in res:
+        res[name]["roofline"] = {"bound": "alu", "achieved": res[name]["achieved_tflops"], "peak": peak[name],
+                                 "unit": "TFLOP/s", "frac": res[name]["achieved_tflops"] / peak[name]}
+    return {"workload": "incomplete_batch64_n4096_m3072_k16_l16384", "unit": "evaluations/s",
+            "value": res["mixed_df"]["evaluations_per_s"], "paths": res, "flops_per_launch": flops,
+            "headline_over_fp64": res["mixed_df"]["evaluations_per_s"] / res["fp64"]["evaluations_per_s"],
+            "fit": fits, "fit_headline_over_fp64": (fits["mixed_df"]["fitted_instances_per_s"]
+                                                    / fits["fp64"]["fitted_instances_per_s"])}
+
+
 # -------------------------------------------------------------- GPU arm ---
 def main():
     ap = argparse.ArgumentParser()
@@ -598,6 +711,7 @@ def main():
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged 1024-instance graph launch")
     ap.add_argument("--no-c3", action="store_true", help="skip the N = 65536 eval-grid leg")
     ap.add_argument("--no-mmv", action="store_true", help="skip the multiple-measurement-vector leg")
+    ap.add_argument("--no-semifast", action="store_true", help="skip the incomplete-data (semifast) leg")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -770,6 +884,8 @@ def main():
     c3 = c3_grid_leg(lse, dev, args.steps, args.warmup, flush) if not args.no_c3 and rank == 0 else None
     progress("multiple-measurement-vector leg")
     mmv = mmv_leg(lse, dev, args.steps, args.warmup, flush) if not args.no_mmv and rank == 0 else None
+    progress("incomplete-data (semifast) leg")
+    semifast = semifast_leg(lse, dev, args.steps, args.warmup, flush) if not args.no_semifast and rank == 0 else None
     progress("serving leg")
     serving = serve_leg(lse, args.serve_seconds, local) if args.serve_seconds > 0 and rank == 0 else None
 
@@ -836,6 +952,7 @@ def main():
                           "algorithmic_bytes": "(16 N + 36 L) per instance", "peak_source": peak_src},
         "c3_grid": c3,
         "mmv": mmv,
+        "semifast": semifast,
         "fit": {"iters_mean": float(np.mean(m["iters"])), "n_evals_mean": float(np.mean(m["n_evals"])),
                 "n_grid_mean": float(np.mean(m["n_grid"])), "K_mean": float(np.mean(m["K"])),
                 "status_nonzero": int(np.count_nonzero(m["status"])), "fit_kernel_ms": m["kernel_ms"]},

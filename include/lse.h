@@ -364,6 +364,68 @@ LSE_API lse_status lse_eval_grid_batch_d(lse_ctx* ctx, const float* y_d, const i
                                  const int32_t* L, int32_t dtype, void* q, void* dq, void* d2q,
                                  void* s, void* ds, void* d2s, void* stream);
 
+/* ---- Incomplete observations: the semifast evaluation (Sec. IV) ---------
+ * Instance b observes M_b = m_offsets[b+1] - m_offsets[b] samples
+ * y_m = z(n_m) of an N[b]-sample signal (Phi a row selection; obs_d holds
+ * the indices n_m, ascending, in [0, N[b])).  At the state (theta, gamma,
+ * beta) of its K_b components (as for lse_eval_grid_batch_d) C is the
+ * M_b x M_b matrix beta I + A Gamma A^H with A = Phi Psi(theta) (eq. py), and
+ * the evaluation follows Sec. IV: Woodbury's identity (eq. CfromSigma) with
+ * one K_b x K_b Cholesky factorisation of Sigma^{-1} = A^H A / beta +
+ * Gamma^{-1}, the K_b x K_b matrices A_{D^a}^H A of eq. (AhA) and the sums
+ * A_{D^a}^H y by a non-uniform FFT, the grid q by an L-point FFT and the grid
+ * s by the O(L K^2) contraction.  Outputs (device, written per instance):
+ *   scal_d[2b] = ln|C| (matrix determinant lemma), scal_d[2b+1] = y^H C^{-1} y;
+ *   vec_d: 14 doubles per component, complex q, r, u, s, t, v, x of eqs.
+ *   (q)-(x) (s and x real, imaginary parts 0) at component k of instance b
+ *   starting at double 14 (k_offsets[b] + k);
+ *   q (complex) and s (real) on theta_l = l/L[b], instance b at the prefix
+ *   sum of L as in lse_eval_grid_batch_d, element type dtype (LSE_F64 for an
+ *   LSE_PREC_FP64 context, LSE_F32 otherwise); either may be NULL (both
+ *   NULL: no grid);
+ *   status_d[b] = LSE_OK, or LSE_ENUMERIC if Sigma^{-1} is not numerically
+ *   positive definite.
+ * y_d: device complex64 [2 sum M]; obs_d: device int32 [sum M];
+ * m_offsets, N, k_offsets, L: HOST arrays.  0 <= K_b <= min(M_b, 96),
+ * 1 <= M_b <= N[b] <= 131072, L[b] a power of two >= 2 N[b].  The K x K
+ * algebra is FP64; the transforms, interpolations and the grid contraction
+ * are FP64 on an LSE_PREC_FP64 context and double-float otherwise.
+ * Asynchronous on stream as lse_eval_grid_batch_d (kernel time: which = 1 of
+ * lse_kernel_time). */
+LSE_API lse_status lse_eval_semifast_batch_d(lse_ctx* ctx, const float* y_d, const int32_t* obs_d,
+                                             const int64_t* m_offsets, int32_t B, const int32_t* N,
+                                             const double* theta_d, const double* gamma_d,
+                                             const int64_t* k_offsets, const double* beta_d, const int32_t* L,
+                                             int32_t dtype, double* scal_d, double* vec_d, void* q, void* s,
+                                             int32_t* status_d, void* stream);
+
+/* Fit instances from incomplete observations (Sec. II with the semifast
+ * evaluation of Sec. IV for every model evaluation).  Instance b observes
+ * M_b = m_offsets[b+1] - m_offsets[b] samples of an N[b]-sample signal at
+ * the distinct indices obs_d[m_offsets[b] ..] (ascending, in [0, N[b])).
+ * The estimator is lse_fit's with M where the paper counts observations
+ * (K_max = M, zeta = K/M, beta divided by M, the M 1e-7 and M 1e-8
+ * thresholds of Sec. II-D) and N where it measures resolution ((50N)^2,
+ * 0.05/N); grid values are FP64-class on every path, so grid decisions are
+ * taken on them directly.  At most min(M, 96) components are activated.
+ * y_d: device complex64 [2 sum M]; obs_d: device int32 [sum M]; m_offsets,
+ * N: HOST arrays; out: device arrays as in lse_batch_out with instance b's
+ * theta, gamma, alpha slice at m_offsets[b].  L per instance: cfg->grid_size,
+ * or 8 N rounded to the nearest power of two.  FP64 arithmetic on an
+ * LSE_PREC_FP64 context, double-float (with FP64 K x K algebra) otherwise.
+ * Asynchronous on stream (NULL = the context's stream); kernel time: which
+ * = 0 of lse_kernel_time.  An index outside [0, N) ends that instance with
+ * LSE_EINVAL. */
+LSE_API lse_status lse_fit_incomplete_batch_d(lse_ctx* ctx, const float* y_d, const int32_t* obs_d,
+                                              const int64_t* m_offsets, int32_t B, const int32_t* N,
+                                              const lse_batch_out* out, void* stream);
+
+/* One instance of lse_fit_incomplete_batch_d from host arrays: y complex64
+ * [2 M], obs int32 [M]; out as for lse_fit (K_cap set by the caller).
+ * Returns the instance's status.  Blocks until done. */
+LSE_API lse_status lse_fit_incomplete(lse_ctx* ctx, const float* y, const int32_t* obs, int32_t M, int32_t N,
+                                      lse_result* out);
+
 /* Device time of this context's kernels, from CUDA events recorded on the
  * launch stream around every launch since the previous call.  which: 0 = fit
  * kernel, 1 = factorisation kernel (first column, Levinson recursion,

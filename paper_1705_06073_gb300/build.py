@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblse.so")
-UNITS = ["lse_api.cu", "lse_fit.cu", "lse_grid.cu", "lse_noalloc.cu", "lse_serve.cu"]
+UNITS = ["lse_api.cu", "lse_fit.cu", "lse_grid.cu", "lse_noalloc.cu", "lse_serve.cu", "lse_semifast.cu"]
 
 
 def _nvcc() -> str:

@@ -53,8 +53,8 @@ struct lse_ctx {
   c64* tw32 = nullptr;
   float4* twdf = nullptr;
   int log2max = 0;
-  DevBuf ws, counter, stage_in, stage_out, fac;
-  Staged fit_meta, grid_meta;
+  DevBuf ws, counter, stage_in, stage_out, fac, semi;
+  Staged fit_meta, grid_meta, semi_meta;
   size_t allocated = 0;
   std::vector<TimedLaunch> timed[3];
   std::string err;
@@ -76,6 +76,9 @@ namespace {
 
 // snapshots per instance accepted by the multiple-measurement-vector fits
 constexpr int32_t kMaxSnapshots = 1024;
+// components per instance accepted by the semifast evaluation (its K x K
+// factor is staged in shared memory for the grid contraction)
+constexpr int32_t kMaxSemifastK = 96;
 
 lse_status fail(lse_ctx* c, lse_status s, const std::string& msg) {
   if (c) c->err = msg;
@@ -385,10 +388,11 @@ void lse_destroy(lse_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->cfg.device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  for (DevBuf* b : {&ctx->ws, &ctx->counter, &ctx->stage_in, &ctx->stage_out, &ctx->fac})
+  for (DevBuf* b : {&ctx->ws, &ctx->counter, &ctx->stage_in, &ctx->stage_out, &ctx->fac, &ctx->semi})
     if (b->p) cudaFree(b->p);
   release(ctx->fit_meta);
   release(ctx->grid_meta);
+  release(ctx->semi_meta);
   if (ctx->tw64) cudaFree(ctx->tw64);
   if (ctx->tw32) cudaFree(ctx->tw32);
   if (ctx->twdf) cudaFree(ctx->twdf);
@@ -656,6 +660,164 @@ lse_status lse_fit(lse_ctx* ctx, const float* y, int32_t N, lse_result* out) {
   lse_status per = LSE_OK;
   lse_status s = lse_fit_batch(ctx, y, off, 1, out, &per);
   return s ? s : per;
+}
+
+lse_status lse_eval_semifast_batch_d(lse_ctx* ctx, const float* y_d, const int32_t* obs_d, const int64_t* m_offsets,
+                                     int32_t B, const int32_t* N, const double* theta_d, const double* gamma_d,
+                                     const int64_t* k_offsets, const double* beta_d, const int32_t* L, int32_t dtype,
+                                     double* scal_d, double* vec_d, void* q, void* s, int32_t* status_d,
+                                     void* stream) {
+  if (!ctx || !y_d || !obs_d || !m_offsets || !N || !k_offsets || !beta_d || !L || !scal_d || !vec_d ||
+      !status_d || B < 1)
+    return fail(ctx, LSE_EINVAL, "null argument or B < 1");
+  if (m_offsets[0] != 0 || k_offsets[0] != 0) return fail(ctx, LSE_EINVAL, "offsets must start at 0");
+  const bool f64 = ctx->cfg.precision == LSE_PREC_FP64;
+  if (dtype != (f64 ? LSE_F64 : LSE_F32))
+    return fail(ctx, LSE_EINVAL, "dtype must be LSE_F64 for an FP64 context and LSE_F32 for a mixed one");
+  cudaSetDevice(ctx->cfg.device);
+  cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+  const bool cap = is_capturing(st);
+  std::vector<SemiDesc> d(B);
+  int Nmax = 0, Lmax = 0, Kmax = 0, rmax = 1;
+  int64_t g = 0;
+  for (int b = 0; b < B; ++b) {
+    const int64_t m = m_offsets[b + 1] - m_offsets[b];
+    const int64_t k = k_offsets[b + 1] - k_offsets[b];
+    if (N[b] < 2 || N[b] > (1 << 17) || m < 1 || m > N[b])
+      return fail(ctx, LSE_EINVAL, "instance " + std::to_string(b) + ": N or M out of range");
+    if (k < 0 || k > kMaxSemifastK || k > m)
+      return fail(ctx, LSE_EINVAL, "instance " + std::to_string(b) + ": K must be in [0, min(M, " +
+                                       std::to_string(kMaxSemifastK) + ")]");
+    if (!is_pow2(L[b]) || L[b] < 2 * N[b]) return fail(ctx, LSE_EINVAL, "L must be a power of two >= 2N");
+    d[b] = SemiDesc{m_offsets[b], (int)m, N[b], L[b], (int)k, k_offsets[b], g, b};
+    g += L[b];
+    Nmax = std::max(Nmax, N[b]);
+    Lmax = std::max(Lmax, L[b]);
+    Kmax = std::max(Kmax, (int)k);
+    rmax = std::max(rmax, L[b] / (1 << ilog2(2u * (uint32_t)N[b])));
+  }
+  const int log2t = std::max(ilog2((uint32_t)Lmax), ilog2(2u * (uint32_t)Nmax));
+  if (cap && (!ctx->tw64 || ctx->log2max < log2t))
+    return fail(ctx, LSE_EINVAL, "twiddle tables must grow, which cannot be captured: make one call first");
+  lse_status sst = ensure_tables(ctx, log2t);
+  if (sst) return sst;
+  const size_t per = semifast_workspace_bytes(Kmax, Nmax, Lmax);
+  if ((sst = ensure(ctx, ctx->semi, per * (size_t)B, cap))) return sst;
+  if (!cap && st != ctx->stream && (sst = order_after(ctx, st, ctx->stream))) return sst;
+  if ((sst = stage(ctx, ctx->semi_meta, d.data(), d.size() * sizeof(SemiDesc), st, cap))) return sst;
+  const size_t smem = semifast_smem_bytes(Kmax, rmax);
+  if (smem > 200 * 1024) return fail(ctx, LSE_EINVAL, "K too large for the semifast kernel's shared memory");
+  record(ctx, 1, st, true);
+  const cudaError_t e = launch_semifast(!f64, y_d, obs_d, (const SemiDesc*)ctx->semi_meta.dev.p, B, Kmax, Nmax, Lmax,
+                                        theta_d, gamma_d, beta_d, tables(ctx), ctx->semi.p, scal_d, (c128*)vec_d, q,
+                                        s, f64, status_d, smem, st);
+  record(ctx, 1, st, false);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "semifast kernel launch");
+  if (!cap && st != ctx->stream && (sst = order_after(ctx, ctx->stream, st))) return sst;
+  return LSE_OK;
+}
+
+lse_status lse_fit_incomplete_batch_d(lse_ctx* ctx, const float* y_d, const int32_t* obs_d, const int64_t* m_offsets,
+                                      int32_t B, const int32_t* N, const lse_batch_out* out, void* stream) {
+  if (!ctx || !y_d || !obs_d || !m_offsets || !N || !out || B < 1) return fail(ctx, LSE_EINVAL, "null argument or B < 1");
+  if (m_offsets[0] != 0) return fail(ctx, LSE_EINVAL, "m_offsets[0] must be 0");
+  cudaSetDevice(ctx->cfg.device);
+  cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+  const bool cap = is_capturing(st);
+  std::vector<SemiDesc> d(B);
+  int Nmax = 0, Lmax = 0, rmax = 1;
+  for (int b = 0; b < B; ++b) {
+    const int64_t m = m_offsets[b + 1] - m_offsets[b];
+    if (N[b] < 2 || N[b] > (1 << 17) || m < 1 || m > N[b])
+      return fail(ctx, LSE_EINVAL, "instance " + std::to_string(b) + ": N or M out of range");
+    const int L = ctx->cfg.grid_size ? ctx->cfg.grid_size : default_L(N[b]);
+    if (L < 2 * N[b]) return fail(ctx, LSE_EINVAL, "grid size L must be >= 2N");
+    d[b] = SemiDesc{m_offsets[b], (int)m, N[b], L, 0, 0, 0, b};
+    Nmax = std::max(Nmax, N[b]);
+    Lmax = std::max(Lmax, L);
+    rmax = std::max(rmax, L / (1 << ilog2(2u * (uint32_t)N[b])));
+  }
+  // largest first, as the complete-data batches
+  std::stable_sort(d.begin(), d.end(), [](const SemiDesc& a, const SemiDesc& b) { return a.N > b.N; });
+  const int log2t = std::max(ilog2((uint32_t)Lmax), ilog2(2u * (uint32_t)Nmax));
+  if (cap && (!ctx->tw64 || ctx->log2max < log2t))
+    return fail(ctx, LSE_EINVAL, "twiddle tables must grow, which cannot be captured: make one call first");
+  lse_status sst = ensure_tables(ctx, log2t);
+  if (sst) return sst;
+  const int grid = std::min(B, ctx->sm_count);
+  const size_t per = semifast_fit_workspace_bytes(kMaxSemifastK, Nmax, Lmax);
+  if ((sst = ensure(ctx, ctx->semi, per * (size_t)grid, cap))) return sst;
+  if (!cap && st != ctx->stream && (sst = order_after(ctx, st, ctx->stream))) return sst;
+  if ((sst = stage(ctx, ctx->semi_meta, d.data(), d.size() * sizeof(SemiDesc), st, cap))) return sst;
+  LSE_CUDA(ctx, cudaMemsetAsync(ctx->counter.p, 0, sizeof(int), st));
+  const FitConfig fc{ctx->cfg.tau, ctx->cfg.max_outer, ctx->cfg.max_inner, ctx->cfg.approx_activation_iters, 0, 0,
+                     0, 1, 0};
+  const FitOut fo{out->theta, out->gamma, (c128*)out->alpha, out->K, out->beta, out->objective, out->iters,
+                  out->n_evals, out->n_grid, out->status};
+  const size_t smem = semifast_smem_bytes(kMaxSemifastK, rmax);
+  record(ctx, 0, st, true);
+  const cudaError_t e = launch_semifast_fit(ctx->cfg.precision != LSE_PREC_FP64, y_d, obs_d,
+                                            (const SemiDesc*)ctx->semi_meta.dev.p, B, kMaxSemifastK, Nmax, Lmax, fc,
+                                            tables(ctx), fo, ctx->semi.p, (int*)ctx->counter.p, grid, smem, st);
+  record(ctx, 0, st, false);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "semifast fit kernel launch");
+  if (!cap && st != ctx->stream && (sst = order_after(ctx, ctx->stream, st))) return sst;
+  return LSE_OK;
+}
+
+lse_status lse_fit_incomplete(lse_ctx* ctx, const float* y, const int32_t* obs, int32_t M, int32_t N,
+                              lse_result* out) {
+  if (!ctx || !y || !obs || !out || M < 1 || N < 2 || M > N) return fail(ctx, LSE_EINVAL, "null argument or M, N out of range");
+  cudaSetDevice(ctx->cfg.device);
+  const size_t yb = (size_t)M * 2 * sizeof(float), ib = (size_t)M * sizeof(int32_t);
+  const size_t ob = (size_t)M * 4 * sizeof(double) + 2 * sizeof(double) + 5 * sizeof(int32_t) + 256;
+  lse_status s;
+  if ((s = ensure(ctx, ctx->stage_in, yb + ib + 256))) return s;
+  if ((s = ensure(ctx, ctx->stage_out, ob))) return s;
+  char* in = (char*)ctx->stage_in.p;
+  char* o = (char*)ctx->stage_out.p;
+  lse_batch_out bo;
+  bo.theta = (double*)o; o += M * sizeof(double);
+  bo.gamma = (double*)o; o += M * sizeof(double);
+  bo.alpha = (double*)o; o += M * 2 * sizeof(double);
+  bo.beta = (double*)o; o += sizeof(double);
+  bo.objective = (double*)o; o += sizeof(double);
+  bo.K = (int32_t*)o; o += sizeof(int32_t);
+  bo.iters = (int32_t*)o; o += sizeof(int32_t);
+  bo.n_evals = (int32_t*)o; o += sizeof(int32_t);
+  bo.n_grid = (int32_t*)o; o += sizeof(int32_t);
+  bo.status = (int32_t*)o;
+  const size_t obs_off = (yb + 255) & ~size_t(255);
+  LSE_CUDA(ctx, cudaMemcpyAsync(in, y, yb, cudaMemcpyHostToDevice, ctx->stream));
+  LSE_CUDA(ctx, cudaMemcpyAsync(in + obs_off, obs, ib, cudaMemcpyHostToDevice, ctx->stream));
+  const int64_t offs[2] = {0, M};
+  if ((s = lse_fit_incomplete_batch_d(ctx, (const float*)in, (const int32_t*)(in + obs_off), offs, 1, &N, &bo,
+                                      ctx->stream)))
+    return s;
+  std::vector<char> host(ob);
+  LSE_CUDA(ctx, cudaMemcpyAsync(host.data(), ctx->stage_out.p, ob, cudaMemcpyDeviceToHost, ctx->stream));
+  LSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const char* h = host.data();
+  const double* th = (const double*)h;
+  const double* ga = th + M;
+  const double* al = ga + M;
+  const double* be = al + 2 * (size_t)M;
+  const int32_t* ii = (const int32_t*)(be + 2);
+  const int32_t K = ii[0];
+  out->K = K;
+  out->beta = be[0];
+  out->objective = be[1];
+  out->iters = ii[1];
+  out->n_evals = ii[2];
+  out->n_grid = ii[3];
+  lse_status st = (lse_status)ii[4];
+  if (K > out->K_cap) return LSE_ECAPACITY;
+  for (int k = 0; k < K; ++k) {
+    if (out->theta) out->theta[k] = th[k];
+    if (out->gamma) out->gamma[k] = ga[k];
+    if (out->alpha) { out->alpha[2 * k] = al[2 * k]; out->alpha[2 * k + 1] = al[2 * k + 1]; }
+  }
+  return st;
 }
 
 lse_status lse_eval_grid_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* y_offsets, int32_t B,

@@ -113,6 +113,26 @@ cudaError_t launch_grid(int variant, bool f32, const InstDesc* inst, int Lmax_sm
 // `out` needs 5 B entries; returns the count.
 int grid_tasks(const InstDesc* inst, int B, bool f32, bool q, bool dq, bool d2q, bool s, bool ds, bool d2s, int4* out,
                int* n_small, size_t* ws_elems);
+// Semifast evaluation (incomplete observations, Sec. IV): one instance of a
+// batched launch.
+struct SemiDesc {
+  int64_t m_off;  // offset of y and obs (elements)
+  int32_t M, N, L, K;
+  int64_t k_off;  // offset of the components
+  int64_t g_off;  // offset of the grid outputs
+  int32_t idx;    // instance index (scalars, status)
+};
+size_t semifast_workspace_bytes(int Kmax, int Nmax, int Lmax);
+size_t semifast_fit_workspace_bytes(int Kcap, int Nmax, int Lmax);
+cudaError_t launch_semifast_fit(bool df, const float* y, const int* obs, const SemiDesc* inst, int B, int Kcap,
+                                int Nmax, int Lmax, const FitConfig& cfg, const Tables& tab, const FitOut& out,
+                                void* ws, int* counter, int grid, size_t smem, cudaStream_t stream);
+size_t semifast_smem_bytes(int Kmax, int r_max);
+cudaError_t launch_semifast(bool df, const float* y, const int* obs, const SemiDesc* inst, int B, int Kmax, int Nmax,
+                            int Lmax, const double* theta, const double* gamma, const double* beta, const Tables& tab,
+                            void* ws, double* scal, c128* vec, void* qg, void* sg, bool f64_out, int* status,
+                            size_t smem, cudaStream_t stream);
+
 // whether a grid of size L fits the on-chip FFT kernel
 bool grid_on_chip(bool f32, int L);
 size_t grid_workspace_bytes(size_t ws_elems, bool f32);

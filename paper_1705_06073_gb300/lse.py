@@ -61,7 +61,8 @@ EXPORTS = ["lse_config_default", "lse_create", "lse_destroy", "lse_strerror", "l
            "lse_fit_batch", "lse_fit_batch_d", "lse_eval_grid", "lse_eval_grid_batch_d", "lse_kernel_time",
            "lse_plan_fit", "lse_plan_launch", "lse_plan_graph_launch", "lse_plan_destroy", "lse_serve_create",
            "lse_serve_submit", "lse_serve_poll", "lse_serve_in_flight", "lse_serve_device_bytes", "lse_serve_destroy",
-           "lse_fit_mmv", "lse_fit_mmv_batch_d", "lse_serve_reserve"]
+           "lse_fit_mmv", "lse_fit_mmv_batch_d", "lse_serve_reserve", "lse_eval_semifast_batch_d",
+           "lse_fit_incomplete", "lse_fit_incomplete_batch_d"]
 
 _lib = None
 
@@ -105,6 +106,12 @@ def load(path: str = LIB_PATH):
         "lse_serve_device_bytes": (ctypes.c_uint64, [P]),
         "lse_serve_destroy": (None, [P]),
         "lse_serve_reserve": (ctypes.c_int, [P, ctypes.c_int32]),
+        "lse_fit_incomplete": (ctypes.c_int, [P, c_float_p, c_int32_p, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.POINTER(lse_result)]),
+        "lse_fit_incomplete_batch_d": (ctypes.c_int, [P, P, P, c_int64_p, ctypes.c_int32, c_int32_p,
+                                                      ctypes.POINTER(lse_batch_out), P]),
+        "lse_eval_semifast_batch_d": (ctypes.c_int, [P, P, P, c_int64_p, ctypes.c_int32, c_int32_p, P, P, c_int64_p,
+                                                     P, c_int32_p, ctypes.c_int32, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -336,6 +343,63 @@ def lse_eval_grid_batch_d(ctx, y_d, y_offsets, theta_d, gamma_d, k_offsets, beta
                                       ctypes.c_void_p(gamma_d.data_ptr()), _ptr(k_offsets, c_int64_p),
                                       ctypes.c_void_p(beta_d.data_ptr()), _ptr(L, c_int32_p),
                                       LSE_F64 if f64 else LSE_F32, *p, s)
+    _check(ctx, st)
+
+
+def lse_fit_incomplete(ctx, y, obs, N: int, K_cap: int | None = None) -> dict:
+    """Fit one instance observed at the indices obs (Sec. IV setting): y the
+    observed samples (complex), obs their indices in [0, N)."""
+    y = _c64(y)
+    obs = np.ascontiguousarray(np.asarray(obs, dtype=np.int32))
+    M = y.shape[0]
+    cap = M if K_cap is None else K_cap
+    th = np.zeros(cap)
+    ga = np.zeros(cap)
+    al = np.zeros(2 * cap)
+    r = lse_result()
+    r.K_cap = cap
+    r.theta = _ptr(th, c_double_p)
+    r.gamma = _ptr(ga, c_double_p)
+    r.alpha = _ptr(al, c_double_p)
+    st = load().lse_fit_incomplete(ctx, y.view(np.float32).ctypes.data_as(c_float_p), _ptr(obs, c_int32_p), M, int(N),
+                                   ctypes.byref(r))
+    if st not in (LSE_OK, LSE_ENOTCONV):
+        _check(ctx, st)
+    K = r.K
+    return dict(K=K, theta=th[:K].copy(), gamma=ga[:K].copy(), alpha=al[0:2 * K:2] + 1j * al[1:2 * K:2], beta=r.beta,
+                objective=r.objective, iters=r.iters, n_evals=r.n_evals, n_grid=r.n_grid, status=int(st))
+
+
+def lse_fit_incomplete_batch_d(ctx, y_d, obs_d, m_offsets, N, out: dict, stream=None) -> None:
+    """Device batched fit of incomplete-data instances: torch CUDA tensors
+    y_d (complex64) and obs_d (int32), host m_offsets [B+1] and N [B], out
+    as from alloc_batch_out(m_offsets)."""
+    m_offsets = np.ascontiguousarray(m_offsets, dtype=np.int64)
+    N = np.ascontiguousarray(N, dtype=np.int32)
+    bo = _batch_out(out)
+    s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    st = load().lse_fit_incomplete_batch_d(ctx, ctypes.c_void_p(y_d.data_ptr()), ctypes.c_void_p(obs_d.data_ptr()),
+                                           _ptr(m_offsets, c_int64_p), len(m_offsets) - 1, _ptr(N, c_int32_p),
+                                           ctypes.byref(bo), s)
+    _check(ctx, st)
+
+
+def lse_eval_semifast_batch_d(ctx, y_d, obs_d, m_offsets, N, theta_d, gamma_d, k_offsets, beta_d, L, scal_d, vec_d,
+                              status_d, q=None, s=None, f64: bool = True, stream=None) -> None:
+    """Semifast evaluation of incomplete observations (Sec. IV): torch CUDA
+    tensors y_d (complex64), obs_d (int32), theta_d, gamma_d, beta_d (float64),
+    scal_d (float64 [2B]), vec_d (complex128 [7 sum K]), status_d (int32 [B]),
+    optional grid outputs q (complex) and s (real); host offsets, N and L."""
+    m_offsets = np.ascontiguousarray(m_offsets, dtype=np.int64)
+    k_offsets = np.ascontiguousarray(k_offsets, dtype=np.int64)
+    N = np.ascontiguousarray(N, dtype=np.int32)
+    L = np.ascontiguousarray(L, dtype=np.int32)
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+    st = load().lse_eval_semifast_batch_d(ctx, ptr(y_d), ptr(obs_d), _ptr(m_offsets, c_int64_p), len(m_offsets) - 1,
+                                          _ptr(N, c_int32_p), ptr(theta_d), ptr(gamma_d), _ptr(k_offsets, c_int64_p),
+                                          ptr(beta_d), _ptr(L, c_int32_p), LSE_F64 if f64 else LSE_F32, ptr(scal_d),
+                                          ptr(vec_d), ptr(q), ptr(s), ptr(status_d),
+                                          ctypes.c_void_p(stream.cuda_stream) if stream is not None else None)
     _check(ctx, st)
 
 
