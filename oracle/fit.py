@@ -44,6 +44,25 @@ R9  beta is updated with s, q and C^{-1}y at the current state and the old beta.
 R10 Output components are sorted by frequency; alpha = gamma * q at the final
     state (footnote to eq. bmu).
 R11 y = 0 is degenerate: the result is K = 0, beta = 0.
+
+With update="lbfgs" step 4a is the paper's own L-BFGS update (Sec. II-C1,
+J = 10 saved pairs) instead of R1's diagonal Newton step:
+L1  The variables are (theta_k, gamma_k) of the active components; the
+    initial inverse Hessian of every iteration is diag(1/h) with h the
+    diagonal Hessian of eqs. (derivative2) and its replacements (R1), as
+    Sec. II-C1 proposes; the direction is -H g by the two-loop recursion
+    (Nocedal and Wright, Numerical Optimization, Alg. 7.4) over the saved
+    pairs (s_i, y_i) = (step, gradient change).
+L2  The same step rule as R1 (length 1 cut to 0.99 of the distance to the
+    first gamma = 0, Armijo backtracking); a pair is saved only when
+    s.y > 0; at most J = 10 pairs, the oldest dropped.
+L3  The memory is emptied whenever the problem changes under it: at the
+    start of step 4 of every outer iteration (beta and possibly the active
+    set changed) and after every deactivation (the paper: the Hessian
+    estimate is reinitialised when the activation variables change).
+L4  The squared Newton decrement of R2 is g.H g with H the L-BFGS inverse
+    Hessian (-g.d), against the same N 1e-8 threshold.
+With no saved pair the direction is R1's diagonal Newton step.
 """
 from __future__ import annotations
 
@@ -253,6 +272,83 @@ def _newton_iteration(st: _State):
     return dec, False
 
 
+def lbfgs_direction(g, h, S, Y):
+    """L1: d = -H g for the L-BFGS inverse Hessian H built from the initial
+    diag(1/h) and the pairs (S[i], Y[i]) (oldest first), by the two-loop
+    recursion."""
+    q = np.array(g, dtype=np.float64)
+    stack = []
+    for s_, y_ in zip(reversed(S), reversed(Y)):
+        rho = 1.0 / float(np.dot(y_, s_))
+        a = rho * float(np.dot(s_, q))
+        q = q - a * y_
+        stack.append((rho, a, s_, y_))
+    r = q / np.asarray(h, dtype=np.float64)
+    for rho, a, s_, y_ in reversed(stack):
+        b = rho * float(np.dot(y_, r))
+        r = r + (a - b) * s_
+    return -r
+
+
+class LbfgsMemory:
+    """L2/L3: the saved pairs and the step waiting for its gradient change."""
+
+    def __init__(self, J: int = 10):
+        self.J = J
+        self.reset()
+
+    def reset(self):
+        self.S, self.Y = [], []
+        self.pending = None  # (step s, gradient before the step)
+
+    def absorb(self, g):
+        """Turn the pending step into a pair with the gradient g after it."""
+        if self.pending is not None:
+            s_, g0 = self.pending
+            y_ = g - g0
+            if float(np.dot(s_, y_)) > 0.0:
+                self.S.append(s_)
+                self.Y.append(y_)
+                if len(self.S) > self.J:
+                    self.S.pop(0)
+                    self.Y.pop(0)
+        self.pending = None
+
+
+def _lbfgs_iteration(st: _State, mem: LbfgsMemory):
+    """L1-L4: one L-BFGS update of (theta, gamma).  Returns (decrement, step taken)."""
+    N = st.N
+    K = st.K
+    vec = st.ev.active_vectors()
+    gt, gg, ht, hg = dn.derivatives(vec, st.gamma, N)
+    ht = np.where(ht > 0.0, ht, (50.0 * N) ** 2)
+    hg = np.where(hg > 0.0, hg, 1.0 / st.gamma ** 2)
+    g = np.concatenate([gt, gg])
+    mem.absorb(g)
+    d = lbfgs_direction(g, np.concatenate([ht, hg]), mem.S, mem.Y)
+    dec = float(-np.dot(g, d))
+    if dec < N * 1e-8:
+        return dec, False
+    dt, dg = d[:K], d[K:]
+    slope = float(np.dot(g, d))
+    alpha = 1.0
+    neg = dg < 0.0
+    if np.any(neg):
+        alpha = min(1.0, 0.99 * float(np.min(st.gamma[neg] / -dg[neg])))
+    f0 = st.ev.data_term()
+    for _ in range(31):
+        th = np.mod(st.theta + alpha * dt, 1.0)
+        th = np.where(th >= 1.0, th - 1.0, th)
+        gm = st.gamma + alpha * dg
+        ev = st.evaluate(th, gm)
+        if ev.data_term() <= f0 + 1e-4 * alpha * slope:
+            st.theta, st.gamma, st.ev = th, gm, ev
+            mem.pending = (alpha * d, g)
+            return dec, True
+        alpha *= 0.5
+    return dec, False
+
+
 def deactivation_pick(stat, threshold: float):
     """Which component one step of the deactivation of Sec. II-C4 removes
     (reading R3): among those whose eq. (deactivate) statistic is below the
@@ -284,8 +380,9 @@ def _deactivation(st: _State):
 
 
 def fit(y, L: int, tau: float = 5.0, max_outer: int = 200, max_inner: int = 5,
-        approx_iters: int = 10, trace: bool = False) -> FitResult:
-    """Run the estimator of Sec. II on y (complete data, K_max = N)."""
+        approx_iters: int = 10, trace: bool = False, update: str = "newton") -> FitResult:
+    """Run the estimator of Sec. II on y (complete data, K_max = N); update is
+    "newton" (R1) or "lbfgs" (L1-L4) for step 4a."""
     y = np.asarray(y, dtype=np.complex128)
     N = y.shape[0]
     tr = [] if trace else None
@@ -320,12 +417,17 @@ def fit(y, L: int, tau: float = 5.0, max_outer: int = 200, max_inner: int = 5,
         st.refresh()
         st.log("beta")
         # step 4
+        mem = LbfgsMemory() if update == "lbfgs" else None
         for _ in range(max_inner):
             if st.K == 0:
                 break
-            dec, _stepped = _newton_iteration(st)
+            if mem is None:
+                dec, _stepped = _newton_iteration(st)
+            else:
+                dec, _stepped = _lbfgs_iteration(st, mem)
             st.log("theta_gamma")
-            _deactivation(st)
+            if _deactivation(st) and mem is not None:
+                mem.reset()
             st.log("deactivate")
             if dec < N * 1e-8:
                 break
