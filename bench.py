@@ -712,6 +712,7 @@ def main():
     ap.add_argument("--no-c3", action="store_true", help="skip the N = 65536 eval-grid leg")
     ap.add_argument("--no-mmv", action="store_true", help="skip the multiple-measurement-vector leg")
     ap.add_argument("--no-semifast", action="store_true", help="skip the incomplete-data (semifast) leg")
+    ap.add_argument("--no-lbfgs", action="store_true", help="skip the L-BFGS leg")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -812,6 +813,22 @@ def main():
                          value=sum_over_ranks(Bn * args.steps) / (total_ms / 1e3), out=out)
 
     progress("grid legs")
+    # ---- the headline batch with the L-BFGS update of Sec. II-C1 instead of Newton
+    lbfgs = None
+    if not args.no_lbfgs:
+        ctx_l = lse.lse_create(lse.lse_config_default(device=local, precision=precs[HEAD], grid_size=L,
+                                                      flags=lse.LSE_FLAG_LBFGS))
+        try:
+            out_l = lse.alloc_batch_out(offsets, device=dev)
+            ms_l, kms_l, nl_l = timed_fit(ctx_l, args.steps, args.warmup, out_l)
+            tot_l = max_over_ranks(sum(ms_l))
+            lbfgs = {"value": sum_over_ranks(Bn * args.steps) / (tot_l / 1e3), "unit": "fitted instances/s",
+                     "ms_per_step": tot_l / args.steps, "n_evals_mean": float(out_l["n_evals"].float().mean().item()),
+                     "iters_mean": float(out_l["iters"].float().mean().item()),
+                     "K_mean": float(out_l["K"].float().mean().item())}
+        finally:
+            lse.lse_destroy(ctx_l)
+
     # ---- grid-point throughput at the fitted states (factor + grid kernels)
     grid = {}
     for name, prec in paths:
@@ -953,6 +970,7 @@ def main():
         "c3_grid": c3,
         "mmv": mmv,
         "semifast": semifast,
+        "lbfgs": lbfgs,
         "fit": {"iters_mean": float(np.mean(m["iters"])), "n_evals_mean": float(np.mean(m["n_evals"])),
                 "n_grid_mean": float(np.mean(m["n_grid"])), "K_mean": float(np.mean(m["K"])),
                 "status_nonzero": int(np.count_nonzero(m["status"])), "fit_kernel_ms": m["kernel_ms"]},

@@ -125,6 +125,18 @@ typedef struct lse_config {
  * (about 1e-14 of sum |f_n|). */
 #define LSE_FLAG_DIRECT_SUMS 8u
 
+/* Take step 4a of the estimator (the (theta, gamma) update, Sec. II-D) as one
+ * L-BFGS update, the paper's own choice (Sec. II-C1, J = 10 saved pairs),
+ * instead of the default per-component diagonal Newton step: the initial
+ * inverse Hessian of every update is the diagonal of eqs. (derivative2) with
+ * its replacements ((50N)^2, gamma^-2), the direction comes from the two-loop
+ * recursion over the pairs kept (s.y > 0), the memory is emptied at the start
+ * of step 4 of every outer iteration and whenever a component is removed, and
+ * the stopping decrement is g.H g.  With no pair saved the step is the Newton
+ * one.  Applies to the complete-data fits (single and multiple measurement
+ * vectors); the incomplete-data fits use the Newton step. */
+#define LSE_FLAG_LBFGS 16u
+
 /* Fill cfg with the paper's defaults (device 0, FP64, tau = 5, ...). */
 LSE_API void lse_config_default(lse_config* cfg);
 

@@ -360,7 +360,8 @@ lse_status lse_create(const lse_config* cfg, lse_ctx** out) {
   if (c.precision != LSE_PREC_FP64 && c.precision != LSE_PREC_MIXED && c.precision != LSE_PREC_MIXED_DF)
     return LSE_EINVAL;
   if (c.max_outer < 1 || c.max_inner < 0 || c.approx_activation_iters < 0 || !(c.tau >= 0.0) ||
-      (c.flags & ~(uint64_t)(LSE_FLAG_NO_AUTOTUNE | LSE_FLAG_NO_CLUSTER | LSE_FLAG_LEVINSON | LSE_FLAG_DIRECT_SUMS)))
+      (c.flags & ~(uint64_t)(LSE_FLAG_NO_AUTOTUNE | LSE_FLAG_NO_CLUSTER | LSE_FLAG_LEVINSON | LSE_FLAG_DIRECT_SUMS |
+                             LSE_FLAG_LBFGS)))
     return LSE_EINVAL;
   if (c.grid_size < 0 || (c.grid_size > 0 && !is_pow2(c.grid_size))) return LSE_EINVAL;
   int ndev = 0;
@@ -452,7 +453,8 @@ lse_status fit_batch_d(lse_ctx* ctx, const float* y_d, const int64_t* offsets, i
   LSE_CUDA(ctx, cudaMemsetAsync(ctx->counter.p, 0, sizeof(int), st));
   FitConfig fc{ctx->cfg.tau, ctx->cfg.max_outer, ctx->cfg.max_inner, ctx->cfg.approx_activation_iters,
                !(ctx->cfg.flags & LSE_FLAG_NO_CLUSTER), superfast_min_n(ctx->cfg.flags), Nmin, G,
-               nufft_min_k(ctx->cfg.flags)};
+               nufft_min_k(ctx->cfg.flags),
+               (ctx->cfg.flags & LSE_FLAG_LBFGS) ? 1 : 0};
   FitOut fo{out->theta, out->gamma, (c128*)out->alpha, out->K, out->beta, out->objective, out->iters,
             out->n_evals, out->n_grid, out->status};
   record(ctx, 0, st, true);
@@ -597,7 +599,8 @@ lse_status lse_plan_launch(lse_plan* p, const float* y_d, const lse_batch_out* o
   LSE_CUDA(ctx, cudaMemsetAsync(p->counter.p, 0, sizeof(int), st));
   const FitConfig fc{ctx->cfg.tau, ctx->cfg.max_outer, ctx->cfg.max_inner, ctx->cfg.approx_activation_iters,
                      !(ctx->cfg.flags & LSE_FLAG_NO_CLUSTER), superfast_min_n(ctx->cfg.flags), p->Nmin, 1,
-                     nufft_min_k(ctx->cfg.flags)};
+                     nufft_min_k(ctx->cfg.flags),
+               (ctx->cfg.flags & LSE_FLAG_LBFGS) ? 1 : 0};
   const FitOut fo{out->theta, out->gamma, (c128*)out->alpha, out->K, out->beta, out->objective, out->iters,
                   out->n_evals, out->n_grid, out->status};
   const cudaError_t e = launch_fit(p->prec, y_d, (const InstDesc*)p->desc.p, p->B, p->Nmax, p->Lmax, fc, tables(ctx),

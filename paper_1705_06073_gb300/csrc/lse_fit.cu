@@ -73,6 +73,9 @@ struct FitShared {
   LevShared lev;
   LevCmd cmd;  // cluster mode: request from the first block (lev_send_cmd)
   int sf_bad;  // superfast recursion: a pivot <= 0 or not finite
+  // L-BFGS memory: pairs in a ring of kLbfgsJ, and whether a step awaits its gradient
+  int lb_count, lb_head, lb_pending;
+  double lb_rho[10], lb_a[10];
   int sf_rex[kNT / 32];
   // instance state (written by thread 0, read by all after a barrier)
   int inst, K, status, n_evals, n_grid, cand_count, flag;
@@ -105,6 +108,10 @@ struct Work {
   c128* rs_sums;     // G x 7 kRescore
   float4* sf;        // superfast Schur recursion (schur_workspace_elems(Nmax))
   double* gq2;       // Lmax: sum over snapshots of |q|^2 on the grid (G > 1)
+  // L-BFGS (one base pointer; the arrays are derived where used): the pairs
+  // S and Y (kLbfgsJ x 2 Nmax each), then 2 Nmax each of the gradient, the
+  // diagonal Hessian, the pending step and its gradient
+  double* lb;
   float4* nu;        // 2 (4 + 3G) M2max: transforms of the non-uniform FFT sums
   double* nfac64;    // Nmax: its deconvolution factors (FP64)
   float2* nfacdf;    // Nmax: the same as double-float pairs
@@ -118,9 +125,10 @@ struct Work {
 };
 
 constexpr int kRescore = Work<double>::kRescoreW;  // grid points re-scored in FP64 per batch
+constexpr int kLbfgsJ = 10;  // L-BFGS pairs kept (Sec. II-C1: J = 10)
 
 struct Layout {
-  size_t off[40];
+  size_t off[48];
   size_t total;
 };
 
@@ -151,6 +159,7 @@ __host__ __device__ inline Layout make_layout(int Nmax, int Lmax, int G) {
   put(sizeof(c128) * 7 * (size_t)kRescore * G);                         // rs_sums
   put(sizeof(float4) * schur_workspace_elems(Nmax));                     // sf
   put(G > 1 ? sizeof(double) * (size_t)Lmax : 0);                       // gq2
+  put(sizeof(double) * (2 * kLbfgsJ + 4) * 2 * (size_t)Nmax);           // lb
   put(sizeof(float4) * 2 * (size_t)(4 + 3 * G) * M2);                   // nu
   put(sizeof(double) * (size_t)Nmax);                                   // nfac64
   put(sizeof(float2) * (size_t)Nmax);                                   // nfacdf
@@ -192,6 +201,7 @@ __device__ Work<TG> carve(char* base, int Nmax, int Lmax, int G) {
   w.rs_sums = (c128*)(base + L.off[i++]);
   w.sf = (float4*)(base + L.off[i++]);
   w.gq2 = (double*)(base + L.off[i++]);
+  w.lb = (double*)(base + L.off[i++]);
   w.nu = (float4*)(base + L.off[i++]);
   w.nfac64 = (double*)(base + L.off[i++]);
   w.nfacdf = (float2*)(base + L.off[i++]);
@@ -736,6 +746,150 @@ struct Fitter {
     return dec;
   }
 
+  // ------------------------------------------------------------- L-BFGS ---
+  __device__ double* lb_S() const { return w.lb; }
+  __device__ double* lb_Y() const { return w.lb + (size_t)kLbfgsJ * 2 * A->Nmax; }
+  __device__ double* lb_g() const { return w.lb + (size_t)(2 * kLbfgsJ) * 2 * A->Nmax; }
+  __device__ double* lb_h() const { return w.lb + (size_t)(2 * kLbfgsJ + 1) * 2 * A->Nmax; }
+  __device__ double* lb_ps() const { return w.lb + (size_t)(2 * kLbfgsJ + 2) * 2 * A->Nmax; }
+  __device__ double* lb_pg() const { return w.lb + (size_t)(2 * kLbfgsJ + 3) * 2 * A->Nmax; }
+  // The L-BFGS update of Sec. II-C1 (readings L1-L4 of the oracle): with the
+  // gradient g and the diagonal Hessian h (2K entries, theta then gamma) in
+  // lbg / lbh, first turn a pending step into a pair (kept when s.y > 0, at
+  // most kLbfgsJ, the oldest overwritten), then d = -H g by the two-loop
+  // recursion with H_0 = diag(1/h) into dth / dga; dec = g.H g, slope = g.d.
+  __device__ double dot2(const double* a, const double* b, int n) {
+    double p = 0.0;
+    for (int i = threadIdx.x; i < n; i += kNT) p += a[i] * b[i];
+    return block_sum<kNT>(p, sh->dred);
+  }
+  __device__ void lbfgs_reset() {
+    if (threadIdx.x == 0) {
+      sh->lb_count = 0;
+      sh->lb_head = 0;
+      sh->lb_pending = 0;
+    }
+    __syncthreads();
+  }
+  // one L-BFGS update of (theta, gamma): the step rule of newton_iteration
+  // with the direction of lbfgs_direction; returns g.H g
+  __device__ __noinline__ double lbfgs_iteration() {
+    const int K = sh->K;
+    const double inv_delta = 1.0 / sh->delta_last;
+    const double h_theta_fb = (50.0 * N) * (50.0 * N);
+    for (int k = threadIdx.x; k < K; k += kNT) {
+      const double g = w.gamma[k];
+      Derivs d = objective_derivatives(component_vectors<double>(w.sums + 7 * k, inv_delta), g);
+      for (int gi = 1; gi < G; ++gi) {
+        const Derivs e = objective_derivatives(component_vectors<double>(w.sumsg(gi) + 7 * k, inv_delta), g);
+        d.gt += e.gt;
+        d.gg += e.gg;
+        d.ht += e.ht;
+        d.hg += e.hg;
+      }
+      lb_g()[k] = d.gt;
+      lb_g()[K + k] = d.gg;
+      lb_h()[k] = d.ht > 0.0 ? d.ht : h_theta_fb;
+      lb_h()[K + k] = d.hg > 0.0 ? d.hg : 1.0 / (g * g);
+    }
+    double dec, slope;
+    lbfgs_direction(K, dec, slope);
+    double amax = HUGE_VAL;
+    for (int k = threadIdx.x; k < K; k += kNT)
+      if (w.dga[k] < 0.0) amax = fmin(amax, w.gamma[k] / -w.dga[k]);
+    MinLoc am{amax, 0};
+    am = block_minloc<kNT>(am, sh->ml);
+    if (dec < (double)(G * N) * 1e-8) return dec;
+    double alpha = am.v < HUGE_VAL ? fmin(1.0, 0.99 * am.v) : 1.0;
+    const double f0 = sh->f_cur;
+    for (int j = 0; j < 31; ++j) {
+      for (int k = threadIdx.x; k < K; k += kNT) {
+        w.th_t[k] = mod1(w.theta[k] + alpha * w.dth[k]);
+        w.ga_t[k] = w.gamma[k] + alpha * w.dga[k];
+      }
+      __syncthreads();
+      const int bad = evaluate(w.th_t, w.ga_t, K, false);
+      if (!bad && sh->f_cur <= f0 + 1e-4 * alpha * slope) {
+        for (int k = threadIdx.x; k < K; k += kNT) {
+          w.theta[k] = w.th_t[k];
+          w.gamma[k] = w.ga_t[k];
+          // the step and its gradient wait for the next gradient (a pair)
+          lb_ps()[k] = alpha * w.dth[k];
+          lb_ps()[K + k] = alpha * w.dga[k];
+          lb_pg()[k] = lb_g()[k];
+          lb_pg()[K + k] = lb_g()[K + k];
+        }
+        if (threadIdx.x == 0) sh->lb_pending = 1;
+        __syncthreads();
+        compute_sums(w.theta, K);
+        return dec;
+      }
+      alpha *= 0.5;
+    }
+    if (evaluate(w.theta, w.gamma, K, true)) {
+      if (threadIdx.x == 0) sh->status = kST_NUMERIC;
+      __syncthreads();
+    }
+    return dec;
+  }
+
+  __device__ __noinline__ void lbfgs_direction(int K, double& dec, double& slope) {
+    const int n = 2 * K;
+    const size_t st = 2 * (size_t)A->Nmax;
+    __syncthreads();
+    if (sh->lb_pending) {
+      const int slot = sh->lb_head;
+      double* s_ = lb_S() + slot * st;
+      double* y_ = lb_Y() + slot * st;
+      for (int i = threadIdx.x; i < n; i += kNT) {
+        s_[i] = lb_ps()[i];
+        y_[i] = lb_g()[i] - lb_pg()[i];
+      }
+      __syncthreads();
+      const double sy = dot2(s_, y_, n);
+      if (threadIdx.x == 0) {
+        sh->lb_pending = 0;
+        if (sy > 0.0) {
+          sh->lb_rho[slot] = 1.0 / sy;
+          sh->lb_head = (slot + 1) % kLbfgsJ;
+          sh->lb_count = min(sh->lb_count + 1, kLbfgsJ);
+        }
+      }
+      __syncthreads();
+    }
+    const int cnt = sh->lb_count, head = sh->lb_head;
+    // q = g (in lbps, free now), newest pair first
+    double* q = lb_ps();
+    for (int i = threadIdx.x; i < n; i += kNT) q[i] = lb_g()[i];
+    __syncthreads();
+    for (int t = 0; t < cnt; ++t) {
+      const int slot = (head - 1 - t + kLbfgsJ) % kLbfgsJ;
+      const double* s_ = lb_S() + slot * st;
+      const double* y_ = lb_Y() + slot * st;
+      const double a = sh->lb_rho[slot] * dot2(s_, q, n);
+      if (threadIdx.x == 0) sh->lb_a[slot] = a;
+      for (int i = threadIdx.x; i < n; i += kNT) q[i] -= a * y_[i];
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < n; i += kNT) q[i] /= lb_h()[i];
+    __syncthreads();
+    for (int t = cnt - 1; t >= 0; --t) {
+      const int slot = (head - 1 - t + kLbfgsJ) % kLbfgsJ;
+      const double* s_ = lb_S() + slot * st;
+      const double* y_ = lb_Y() + slot * st;
+      const double b = sh->lb_rho[slot] * dot2(y_, q, n);
+      const double a = sh->lb_a[slot];
+      for (int i = threadIdx.x; i < n; i += kNT) q[i] += (a - b) * s_[i];
+      __syncthreads();
+    }
+    for (int k = threadIdx.x; k < K; k += kNT) {
+      w.dth[k] = -q[k];
+      w.dga[k] = -q[K + k];
+    }
+    dec = dot2(lb_g(), q, n);  // g.H g
+    slope = -dec;
+  }
+
   // ---------------------------------------------------------- deactivation ---
   __device__ void deactivation() {
     while (sh->K > 0 && sh->status == kST_OK) {
@@ -902,11 +1056,15 @@ struct Fitter {
           break;
         }
       }
-      // step 4
+      // step 4 (the L-BFGS memory starts empty, and is emptied again when a
+      // component is removed)
+      if (A->cfg.lbfgs) lbfgs_reset();
       for (int inner = 0; inner < A->cfg.max_inner && sh->status == kST_OK; ++inner) {
         if (sh->K == 0) break;
-        const double dec = newton_iteration();
+        const double dec = A->cfg.lbfgs ? lbfgs_iteration() : newton_iteration();
+        const int K_before = sh->K;
         deactivation();
+        if (A->cfg.lbfgs && sh->K != K_before) lbfgs_reset();
         if (dec < (double)(G * N) * 1e-8) break;
       }
       if (sh->status != kST_OK) break;

@@ -38,6 +38,7 @@ struct FitConfig {
   int Nmin;       // smallest N of the launch
   int G = 1;      // snapshots per instance (multiple measurement vectors, Sec. V)
   int nufft_min_k = 0;  // off-grid sums at >= this many frequencies by the non-uniform FFT (0: never)
+  int lbfgs = 0;        // step 4a by L-BFGS (Sec. II-C1) instead of diagonal Newton
 };
 
 // nufft_min_k for the lse_config flags (LSE_FLAG_DIRECT_SUMS: 0)

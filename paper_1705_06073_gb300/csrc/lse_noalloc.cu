@@ -120,7 +120,8 @@ LSE_API lse_status lse_fit_noalloc_d(const lse_config* cfg, const float* y_d, in
   if (!y_d || !out) return set_err(LSE_EINVAL, "y_d and out must not be NULL");
   if (N < 2 || N > kMaxN) return set_err(LSE_EINVAL, "lse_fit_noalloc_d: N must be in [2, 4096]");
   if (c.grid_size < 0) return set_err(LSE_EINVAL, "lse_fit_noalloc_d: grid_size must be >= 0");
-  if (c.flags & ~(uint64_t)(LSE_FLAG_NO_AUTOTUNE | LSE_FLAG_NO_CLUSTER | LSE_FLAG_LEVINSON | LSE_FLAG_DIRECT_SUMS))
+  if (c.flags & ~(uint64_t)(LSE_FLAG_NO_AUTOTUNE | LSE_FLAG_NO_CLUSTER | LSE_FLAG_LEVINSON | LSE_FLAG_DIRECT_SUMS |
+                            LSE_FLAG_LBFGS))
     return set_err(LSE_EINVAL, "lse_fit_noalloc_d: unknown flag bits");
   const int L = c.grid_size ? c.grid_size : 1 << (int)std::lround(std::log2(8.0 * N));
   if ((L & (L - 1)) || L < 2 * N || L > (1 << kMaxLog2L))
@@ -144,7 +145,7 @@ LSE_API lse_status lse_fit_noalloc_d(const lse_config* cfg, const float* y_d, in
   if (cudaGetLastError() != cudaSuccess)
     return set_err(LSE_ECUDA, "lse_fit_noalloc_d: staging the launch descriptor failed");
   const FitConfig fc{c.tau, c.max_outer, c.max_inner, c.approx_activation_iters, !(c.flags & LSE_FLAG_NO_CLUSTER),
-                     superfast_min_n(c.flags), N, 1, nufft_min_k(c.flags)};
+                     superfast_min_n(c.flags), N, 1, nufft_min_k(c.flags), (c.flags & LSE_FLAG_LBFGS) ? 1 : 0};
   const FitOut fo{out->theta, out->gamma, (c128*)out->alpha, out->K, out->beta, out->objective, out->iters,
                   out->n_evals, out->n_grid, out->status};
   const Tables tab{d->tw64, d->tw32, kMaxLog2L, d->twdf};

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(HERE, "_build", "liblse.so")
 LSE_OK, LSE_EINVAL, LSE_ENOMEM, LSE_EBUDGET, LSE_ENUMERIC, LSE_ENOTCONV, LSE_ETIMEOUT, LSE_ECUDA, LSE_ECAPACITY = range(9)
 LSE_PREC_FP64, LSE_PREC_MIXED, LSE_PREC_MIXED_DF = 0, 1, 2
 LSE_F32, LSE_F64 = 0, 1
-LSE_FLAG_NO_AUTOTUNE, LSE_FLAG_NO_CLUSTER, LSE_FLAG_LEVINSON, LSE_FLAG_DIRECT_SUMS = 1, 2, 4, 8
+LSE_FLAG_NO_AUTOTUNE, LSE_FLAG_NO_CLUSTER, LSE_FLAG_LEVINSON, LSE_FLAG_DIRECT_SUMS, LSE_FLAG_LBFGS = 1, 2, 4, 8, 16
 
 c_double_p = ctypes.POINTER(ctypes.c_double)
 c_int32_p = ctypes.POINTER(ctypes.c_int32)
