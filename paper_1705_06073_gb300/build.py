@@ -16,7 +16,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblse.so")
-UNITS = ["lse_api.cu", "lse_fit.cu", "lse_grid.cu", "lse_noalloc.cu", "lse_serve.cu", "lse_semifast.cu"]
+# (source, object, extra nvcc flags): lse_fit.cu builds as four units, one
+# per kernel precision and one for its host code, so that they compile in
+# parallel
+UNITS = [("lse_api.cu", "lse_api.o", []), ("lse_grid.cu", "lse_grid.o", []),
+         ("lse_noalloc.cu", "lse_noalloc.o", []), ("lse_serve.cu", "lse_serve.o", []),
+         ("lse_semifast.cu", "lse_semifast.o", [])] + [
+    ("lse_fit.cu", f"lse_fit{u}.o", [f"-DLSE_FIT_UNIT={u}"]) for u in range(4)]
 
 
 def _nvcc() -> str:
@@ -53,12 +59,12 @@ def build(verbose: bool = False, force: bool = False) -> str:
     headers = [os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "lse.h"))
     objs, jobs = [], []
-    for u in UNITS:
+    for u, o, extra in UNITS:
         src = os.path.join(SRC, u)
-        obj = os.path.join(OUT, u.replace(".cu", ".o"))
+        obj = os.path.join(OUT, o)
         objs.append(obj)
         if force or not _newer(obj, [src, *headers, __file__]):
-            jobs.append([nvcc, *FLAGS, "-c", src, "-o", obj])
+            jobs.append([nvcc, *FLAGS, *extra, "-c", src, "-o", obj])
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
             res = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))

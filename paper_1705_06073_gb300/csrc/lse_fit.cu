@@ -28,6 +28,11 @@
 //    activation, which the later iterations use.
 //  - eps_beta = 1e-12 ||y||^2/N, eps_L = 2^-52, K_max = N, termination when
 //    the objective changes by less than N 1e-7 over an outer iteration.
+//
+// The file builds as several translation units, so that the three kernel
+// instantiations compile in parallel: LSE_FIT_UNIT = 0, 1, 2 holds the
+// launch of fit_kernel<PREC> for that precision, 3 the host code; left
+// undefined, one unit holds everything.
 #include <cfloat>
 
 #include "../../include/lse.h"
@@ -1171,6 +1176,16 @@ __global__ void __launch_bounds__(threads_for<PREC>(), 1) fit_kernel(FitArgs arg
 
 }  // namespace
 
+#ifndef LSE_FIT_UNIT
+#define LSE_FIT_UNIT 4
+#endif
+
+// launch of fit_kernel<PREC>; args is a FitArgs (a type local to each unit)
+cudaError_t fit_launch_prec0(const void* args, int grid, cudaStream_t stream);
+cudaError_t fit_launch_prec1(const void* args, int grid, cudaStream_t stream);
+cudaError_t fit_launch_prec2(const void* args, int grid, cudaStream_t stream);
+
+#if LSE_FIT_UNIT == 3 || LSE_FIT_UNIT == 4
 int superfast_min_n(uint64_t flags) { return (flags & LSE_FLAG_LEVINSON) ? 0 : kSuperfastMinN; }
 int nufft_min_k(uint64_t flags) { return (flags & LSE_FLAG_DIRECT_SUMS) ? 0 : kNufftMinK; }
 
@@ -1178,6 +1193,7 @@ size_t fit_workspace_bytes(int Nmax, int Lmax, int prec, int G) {
   return prec ? make_layout<float>(Nmax, Lmax, G).total : make_layout<double>(Nmax, Lmax, G).total;
 }
 int fit_smem_bytes() { return kSmemBytes; }
+#endif
 
 template <int PREC>
 static cudaError_t launch_prec(const FitArgs& a, int grid, cudaStream_t stream) {
@@ -1202,6 +1218,23 @@ static cudaError_t launch_prec(const FitArgs& a, int grid, cudaStream_t stream) 
   return cudaGetLastError();
 }
 
+#if LSE_FIT_UNIT == 0 || LSE_FIT_UNIT == 4
+cudaError_t fit_launch_prec0(const void* args, int grid, cudaStream_t stream) {
+  return launch_prec<0>(*static_cast<const FitArgs*>(args), grid, stream);
+}
+#endif
+#if LSE_FIT_UNIT == 1 || LSE_FIT_UNIT == 4
+cudaError_t fit_launch_prec1(const void* args, int grid, cudaStream_t stream) {
+  return launch_prec<1>(*static_cast<const FitArgs*>(args), grid, stream);
+}
+#endif
+#if LSE_FIT_UNIT == 2 || LSE_FIT_UNIT == 4
+cudaError_t fit_launch_prec2(const void* args, int grid, cudaStream_t stream) {
+  return launch_prec<2>(*static_cast<const FitArgs*>(args), grid, stream);
+}
+#endif
+
+#if LSE_FIT_UNIT == 3 || LSE_FIT_UNIT == 4
 cudaError_t launch_fit(int prec, const float* y, const InstDesc* inst, int B, int Nmax, int Lmax,
                        const FitConfig& cfg, const Tables& tab, const FitOut& out, void* ws, int* counter, int grid,
                        cudaStream_t stream) {
@@ -1237,10 +1270,11 @@ cudaError_t launch_fit(int prec, const float* y, const InstDesc* inst, int B, in
     }
   }
   switch (prec) {
-    case 0: return launch_prec<0>(a, grid, stream);
-    case 1: return launch_prec<1>(a, grid, stream);
-    default: return launch_prec<2>(a, grid, stream);
+    case 0: return fit_launch_prec0(&a, grid, stream);
+    case 1: return fit_launch_prec1(&a, grid, stream);
+    default: return fit_launch_prec2(&a, grid, stream);
   }
 }
+#endif
 
 }  // namespace lse
