@@ -70,6 +70,16 @@ __host__ __device__ inline bool lev_in_smem(int N) {
   return (2 * sizeof(c128) * (size_t)N + tab_bytes) <= (size_t)kSmemBytes;
 }
 
+// the superfast recursion's shared-memory part: after the first-column
+// tables of an instance of N samples, with the largest short-run length that fits
+__device__ inline void superfast_smem(char* dsm, int N, float4*& smem, int& lsm) {
+  int S, H;
+  first_column_split(N, S, H);
+  const size_t tb = (sizeof(c128) * kFirstColumnChunk * (S + H) + 255) & ~size_t(255);
+  smem = reinterpret_cast<float4*>(dsm + tb);
+  lsm = schur_pick_lsm(kSmemBytes - tb);
+}
+
 template <int kNT>
 struct FitShared {
   c128 red[kNT];
@@ -272,10 +282,17 @@ struct Fitter {
     else block_first_column<kNT>(lev_c, th, ga, K, beta, N, tables);
     LevResult lr;
     if (superfast()) {
-      if constexpr (PREC == 2)
-        lr = block_superfast<kNT>(PolDF{A->tab.twdf, A->tab.log2max}, lev_c, lev_a, N, w.sf, sf_smem, sf_lsm,
-                                  &sh->sf_bad, sh->dred, sh->sf_rex);
-      else
+      if constexpr (PREC == 2) {
+        if (A->cluster == 2) {  // shared with the other block of the cluster (c, a, w.sf in global memory)
+          if (threadIdx.x == 0) send_cmd(3, N, 0.0, lev_c, lev_a);
+          cluster_barrier();
+          lr = block_superfast<kNT>(PolDF{A->tab.twdf, A->tab.log2max}, lev_c, lev_a, N, w.sf, sf_smem, sf_lsm,
+                                    &sh->sf_bad, sh->dred, sh->sf_rex, 0, 2);
+        } else {
+          lr = block_superfast<kNT>(PolDF{A->tab.twdf, A->tab.log2max}, lev_c, lev_a, N, w.sf, sf_smem, sf_lsm,
+                                    &sh->sf_bad, sh->dred, sh->sf_rex);
+        }
+      } else
         lr = block_superfast<kNT>(Pol64{A->tab.tw64, A->tab.log2max}, lev_c, lev_a, N, w.sf, sf_smem, sf_lsm,
                                   &sh->sf_bad, sh->dred, sh->sf_rex);
     } else if constexpr (PREC == 2) {
@@ -973,13 +990,7 @@ struct Fitter {
       lev_a = w.a;
       tables = (c128*)dsm;
     }
-    {
-      int S, H;
-      first_column_split(N, S, H);
-      const size_t tb = (sizeof(c128) * kFirstColumnChunk * (S + H) + 255) & ~size_t(255);
-      sf_smem = reinterpret_cast<float4*>(dsm + tb);
-      sf_lsm = schur_pick_lsm(kSmemBytes - tb);
-    }
+    superfast_smem(dsm, N, sf_smem, sf_lsm);
     if (threadIdx.x == 0) {
       sh->yy = yy;
       sh->K = 0;
@@ -1111,9 +1122,11 @@ struct Fitter {
 };
 
 // The other blocks of a cluster: they wait for recursion requests from the
-// first block and run their share of each (double-float path only).
+// first block and run their share of each (double-float path only): a
+// Levinson recursion in shared memory (op 1) or global memory (op 2), or the
+// global-memory FFT stages and the refinement of a superfast one (op 3).
 template <int kNT>
-__device__ void cluster_helper(FitShared<kNT>& sh, char* dsm, int csize) {
+__device__ void cluster_helper(FitShared<kNT>& sh, char* dsm, int csize, const FitArgs& args, int unit) {
   for (;;) {
     cluster_barrier();  // a request (or the end) is in sh.cmd
     const int op = sh.cmd.op, n = sh.cmd.N;
@@ -1128,6 +1141,14 @@ __device__ void cluster_helper(FitShared<kNT>& sh, char* dsm, int csize) {
       cluster_levinson_df<kNT>(c, a, n, c0, (float4*)sh.red, &sh.lev);
     } else if (op == 2 && csize == kBigCluster) {
       cluster_levinson_global<kNT, kBigCluster>(sh.cmd.c, sh.cmd.a, n, c0, (float4*)sh.red, &sh.lev);
+    } else if (op == 3 && csize == 2) {
+      float4* smem;
+      int lsm;
+      superfast_smem(dsm, n, smem, lsm);
+      float4* sf = carve<typename Fitter<2>::TG>(args.ws + (size_t)unit * args.ws_bytes, args.Nmax, args.Lmax,
+                                                 args.cfg.G).sf;
+      block_superfast<kNT>(PolDF{args.tab.twdf, args.tab.log2max}, sh.cmd.c, sh.cmd.a, n, sf, smem, lsm, &sh.sf_bad,
+                           sh.dred, sh.sf_rex, 1, 2);
     } else {
       break;
     }
@@ -1144,7 +1165,7 @@ __global__ void __launch_bounds__(threads_for<PREC>(), 1) fit_kernel(FitArgs arg
     if (args.cluster) {
       cluster_barrier();  // both blocks running before any shared-memory store between them
       if (cluster_ctarank() != 0) {
-        cluster_helper<threads_for<PREC>()>(sh, dsm, args.cluster);
+        cluster_helper<threads_for<PREC>()>(sh, dsm, args.cluster, args, (int)(blockIdx.x / args.cluster));
         return;
       }
       unit = blockIdx.x / args.cluster;
@@ -1255,14 +1276,15 @@ cudaError_t launch_fit(int prec, const float* y, const InstDesc* inst, int B, in
   // every instance's recursion fits in shared memory; of kBigCluster blocks,
   // sharing the recursions of the instances too large for shared memory
   // through global memory, when the batch leaves kBigCluster SMs per instance.
+  // Instances that run the superfast recursion share its global-memory FFT
+  // stages and refinement with the second block of a two-block cluster.
   a.cluster = 0;
-  // no clusters when every instance runs the superfast recursion in one block
-  const bool any_levinson = cfg.sf_min_n <= 0 || cfg.Nmin < cfg.sf_min_n || (prec == 2 && !tab.twdf);
-  if (prec == 2 && cfg.cluster && any_levinson) {
+  const bool any_levinson = cfg.sf_min_n <= 0 || cfg.Nmin < cfg.sf_min_n || !tab.twdf;
+  if (prec == 2 && cfg.cluster) {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {
-      if (lev_in_smem(Nmax)) {
+      if (!any_levinson || lev_in_smem(Nmax)) {
         if (2 * grid <= sms) a.cluster = 2;
       } else if (kBigCluster * grid <= sms) {
         a.cluster = kBigCluster;

@@ -106,6 +106,21 @@ struct Pol64 {
   }
 };
 
+// ------------------------------------------------------------- teams -------
+// A recursion can be shared by the blocks of a thread-block cluster (a team of
+// csize blocks, this one of rank crank): the work of a step is split over the
+// team's threads and its steps are separated by cluster barriers (release /
+// acquire at cluster scope, so the global-memory stores of one block are seen
+// by the other).  csize = 1: one block, block barriers.
+__device__ __forceinline__ void team_sync(int csize) {
+  if (csize > 1) cluster_barrier();
+  else __syncthreads();
+}
+// a 32-bit store into the same shared-memory object of block `rank`
+__device__ __forceinline__ void st_cluster_u32(const void* local, unsigned rank, unsigned v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr(local, rank)), "r"(v) : "memory");
+}
+
 // ------------------------------------------------------ batched block FFT --
 // one radix-4 butterfly of a decimation-in-frequency Stockham pass (stride s,
 // group p, offset q), twiddled and stored into out
@@ -132,12 +147,15 @@ __device__ __forceinline__ void pol_bfly4(const Pol& P, typename Pol::T a, typen
 // passes alternate between tmp + j*M and dst + j*M.  inverse: the unscaled
 // inverse transform.  gen must not read dst or tmp.  A thread issues the
 // loads of two butterflies before it computes either, so that in global
-// memory (L2) their latencies overlap.
+// memory (L2) their latencies overlap.  A team of csize blocks (rank crank)
+// splits every pass (gen, dst and tmp then in global memory).
 template <int NT, class Pol, class Gen>
-__device__ __noinline__ void pol_fft(const Pol& P, int nb, Gen gen, float4* dst, float4* tmp, int log2M, bool inverse) {
+__device__ __noinline__ void pol_fft(const Pol& P, int nb, Gen gen, float4* dst, float4* tmp, int log2M, bool inverse,
+                                     int crank = 0, int csize = 1) {
   using T = typename Pol::T;
   constexpr int UN = 2;
   const int M = 1 << log2M;
+  const int g0 = crank * NT + (int)threadIdx.x, S = csize * NT;  // this thread in the team, the team's threads
   const int npass = (log2M >> 1) + (log2M & 1);
   int pass = 0;
   const float4* in = nullptr;
@@ -151,7 +169,7 @@ __device__ __noinline__ void pol_fft(const Pol& P, int nb, Gen gen, float4* dst,
     if (pass == 1) {
       // the first pass reads through gen (which may do its own loads): one
       // butterfly at a time
-      for (int t = threadIdx.x; t < total; t += NT) {
+      for (int t = g0; t < total; t += S) {
         const int j = t >> lq, tt = t & ((1 << lq) - 1);
         const int p = tt >> log2s, q = tt & (s - 1);
         const T a = gen(j, q + s * p), b = gen(j, q + s * (p + n4)), c = gen(j, q + s * (p + 2 * n4)),
@@ -159,11 +177,11 @@ __device__ __noinline__ void pol_fft(const Pol& P, int nb, Gen gen, float4* dst,
         pol_bfly4(P, a, b, c, d, out + (size_t)j * M, p, q, s, log2M, inverse);
       }
     } else {
-      for (int t0 = threadIdx.x; t0 < total; t0 += UN * NT) {
+      for (int t0 = g0; t0 < total; t0 += UN * S) {
         T a[UN], b[UN], c[UN], d[UN];
 #pragma unroll
         for (int u = 0; u < UN; ++u) {
-          const int t = t0 + u * NT;
+          const int t = t0 + u * S;
           if (t < total) {
             const int j = t >> lq, tt = t & ((1 << lq) - 1);
             const int p = tt >> log2s, q = tt & (s - 1);
@@ -174,7 +192,7 @@ __device__ __noinline__ void pol_fft(const Pol& P, int nb, Gen gen, float4* dst,
         }
 #pragma unroll
         for (int u = 0; u < UN; ++u) {
-          const int t = t0 + u * NT;
+          const int t = t0 + u * S;
           if (t < total) {
             const int j = t >> lq, tt = t & ((1 << lq) - 1);
             const int p = tt >> log2s, q = tt & (s - 1);
@@ -183,14 +201,14 @@ __device__ __noinline__ void pol_fft(const Pol& P, int nb, Gen gen, float4* dst,
         }
       }
     }
-    __syncthreads();
+    team_sync(csize);
     in = out;
     n >>= 2; s <<= 2; log2s += 2;
   }
   if (n == 2) {
     ++pass;
     const int lh = log2M - 1;
-    for (int t = threadIdx.x; t < (nb << lh); t += NT) {
+    for (int t = g0; t < (nb << lh); t += S) {
       const int j = t >> lh, q = t & ((1 << lh) - 1);
       T a, b;
       if (pass == 1) {
@@ -203,7 +221,7 @@ __device__ __noinline__ void pol_fft(const Pol& P, int nb, Gen gen, float4* dst,
       Pol::st(oj + q, a + b);
       Pol::st(oj + q + s, a - b);
     }
-    __syncthreads();
+    team_sync(csize);
   }
 }
 
@@ -391,6 +409,12 @@ __device__ __forceinline__ void group_sums(int nout, int nterms, Term term, Stor
 // (2) the second half's Theta transformed and multiplied into the run's.
 // The stack of pending runs is the same in every thread (block-uniform
 // control flow); the buffers of depth k sit at a fixed offset.
+//
+// A team of csize blocks (rank crank): every block walks the same stack; the
+// FFT stages of runs whose buffers are in global memory are shared (a cluster
+// barrier before and after, the passes split), and everything else (leaves,
+// direct sums, runs in shared memory) is done by rank 0 alone, the others
+// skipping it.  The results are those of one block, bit for bit.
 constexpr int kSchurMaxDepth = 16;  // enough for N <= 2^20
 
 struct SchurNode {
@@ -400,17 +424,20 @@ struct SchurNode {
 };
 
 template <int NT, class Pol>
-__device__ __noinline__ void schur_solve(const Pol& Pl, const SchurWork& W, int d0) {
+__device__ __noinline__ void schur_solve(const Pol& Pl, const SchurWork& W, int d0, int crank = 0, int csize = 1) {
   using T = typename Pol::T;
   SchurNode st[kSchurMaxDepth];
   int top = 0;
   st[0] = SchurNode{0, d0, 0, W.Uw, W.Vw, W.Pc, W.Qc};
+  const bool lead = crank == 0;
   while (top >= 0) {
     const SchurNode nd = st[top];
     const int m = nd.m, d = nd.d;
     if (d <= kSchurLeaf) {
-      schur_leaf<Pol>(Pl, W, m, d, nd.Uw, nd.Vw, nd.Pc, nd.Qc);
-      __syncthreads();
+      if (lead) {
+        schur_leaf<Pol>(Pl, W, m, d, nd.Uw, nd.Vw, nd.Pc, nd.Qc);
+        __syncthreads();
+      }
       --top;
       continue;
     }
@@ -419,6 +446,11 @@ __device__ __noinline__ void schur_solve(const Pol& Pl, const SchurWork& W, int 
     const int M = 1 << log2M;
     const int msk = M - 1;
     const bool sm = log2M <= W.lsm;
+    // the team shares the FFT stages of runs kept in global memory
+    const bool team = csize > 1 && !sm && M > Pol::kDirectM;
+    const int tr = team ? crank : 0, ts = team ? csize : 1;
+    const int gt = tr * NT + (int)threadIdx.x, St = ts * NT;  // this thread in the team, the team's threads
+    const bool work = team || lead;
     float4* lev = sm ? W.slevels + schur_level_offset(log2M, W.lsm)
                      : W.levels + schur_level_offset(log2M, ilog2((uint32_t)W.Mtop));
     float4* scr = sm ? W.sscratch : W.scratch;
@@ -436,6 +468,7 @@ __device__ __noinline__ void schur_solve(const Pol& Pl, const SchurWork& W, int 
       continue;
     }
     if (nd.stage == 1 && M <= Pol::kDirectM) {
+      if (lead) {
       // the first half's Theta kept for stage 2 (the second half reuses Pch, Qch)
       for (int i = threadIdx.x; i <= d1; i += NT) {
         Pol::st(F + i, Pol::ld(Pch + i));
@@ -460,12 +493,14 @@ __device__ __noinline__ void schur_solve(const Pol& Pl, const SchurWork& W, int 
           },
           [=] __device__(int o, T v) { Pol::st(o < d2 ? Uh + o : Vh + (o - d2), v); });
       __syncthreads();
+      }
       st[top].stage = 2;
       st[top + 1] = SchurNode{m + d1, d2, 0, Uh, Vh, Pch, Qch};
       ++top;
       continue;
     }
     if (nd.stage == 2 && M <= Pol::kDirectM) {
+      if (lead) {
       // P_i = sum_j P2_j P1_{i-j} + Q2_j conj(Q1_{d1-i+j}),
       // Q_i = sum_j P2_j Q1_{i-j} + Q2_j conj(P1_{d1-i+j})  (P1, Q1 saved in F)
       float4 *Pc = nd.Pc, *Qc = nd.Qc;
@@ -486,10 +521,13 @@ __device__ __noinline__ void schur_solve(const Pol& Pl, const SchurWork& W, int 
             else Pol::st(Pc + o, v);
           });
       __syncthreads();
+      }
       --top;
       continue;
     }
     if (nd.stage == 1) {
+      if (work) {
+      if (team) cluster_barrier();  // the first half (rank 0's, if short) complete
       const float4 *Uw = nd.Uw, *Vw = nd.Vw;
       pol_fft<NT, Pol>(
           Pl, 4,
@@ -499,7 +537,7 @@ __device__ __noinline__ void schur_solve(const Pol& Pl, const SchurWork& W, int 
             if (j == 2) return i < d ? Pol::ld(Uw + i) : Pol::zero();
             return i < d ? Pol::ld(Vw + i) : Pol::zero();
           },
-          F, scr, log2M, false);
+          F, scr, log2M, false, tr, ts);
       // second half's windows: U_h(h+1+s) = (P1 * Uw)[d1+s] + (Q1 * Vw)[d1+1+s],
       // V_h(h+s) = (R1 * Uw)[d1+s-1] + (S1 * Vw)[d1+s]; FFT(R1) = W^{d1 w}
       // conj(F1), FFT(S1) = W^{d1 w} conj(F0), and a shift by one lag is a
@@ -513,25 +551,28 @@ __device__ __noinline__ void schur_solve(const Pol& Pl, const SchurWork& W, int 
             return P2.w((int)(((int64_t)(d1 + 1) * w) & msk), log2M) * (conj(f1) * f2) +
                    P2.w((int)(((int64_t)d1 * w) & msk), log2M) * (conj(f0) * f3);
           },
-          scr, scr + 2 * (size_t)M, log2M, true);
-      for (int s = threadIdx.x; s < d2; s += NT) {
+          scr, scr + 2 * (size_t)M, log2M, true, tr, ts);
+      for (int s = gt; s < d2; s += St) {
         Pol::st(Uh + s, Pol::scale2(inv, Pol::ld(scr + d1 + s)));
         Pol::st(Vh + s, Pol::scale2(inv, Pol::ld(scr + M + d1 + s)));
       }
-      __syncthreads();
+      team_sync(ts);
+      }
       st[top].stage = 2;
       st[top + 1] = SchurNode{m + d1, d2, 0, Uh, Vh, Pch, Qch};
       ++top;
       continue;
     }
     // stage 2: Theta = Theta2 Theta1, P = P2 P1 + Q2 R1, Q = P2 Q1 + Q2 S1
+    if (work) {
+    if (team) cluster_barrier();  // the second half complete
     pol_fft<NT, Pol>(
         Pl, 2,
         [=] __device__(int j, int i) {
           if (j == 0) return i <= d2 ? Pol::ld(Pch + i) : Pol::zero();
           return i <= d2 ? Pol::ld(Qch + i) : Pol::zero();
         },
-        F + 2 * (size_t)M, scr, log2M, false);
+        F + 2 * (size_t)M, scr, log2M, false, tr, ts);
     pol_fft<NT, Pol>(
         Pl, 2,
         [=] __device__(int j, int w) {
@@ -540,9 +581,9 @@ __device__ __noinline__ void schur_solve(const Pol& Pl, const SchurWork& W, int 
           if (j == 0) return g0 * f0 + tw * (g1 * conj(f1));
           return g0 * f1 + tw * (g1 * conj(f0));
         },
-        scr, scr + 2 * (size_t)M, log2M, true);
+        scr, scr + 2 * (size_t)M, log2M, true, tr, ts);
     float4 *Pc = nd.Pc, *Qc = nd.Qc;
-    for (int i = threadIdx.x; i <= d; i += NT) {
+    for (int i = gt; i <= d; i += St) {
       T p = i < M ? Pol::scale2(inv, Pol::ld(scr + i)) : Pol::zero();
       T q = i < M ? Pol::scale2(inv, Pol::ld(scr + M + i)) : Pol::zero();
       if (M == d) {  // coefficient d of Q aliased onto 0 (Q_0 = 0; deg P <= d - 1)
@@ -552,7 +593,8 @@ __device__ __noinline__ void schur_solve(const Pol& Pl, const SchurWork& W, int 
       Pol::st(Pc + i, p);
       Pol::st(Qc + i, q);
     }
-    __syncthreads();
+    team_sync(ts);
+    }
     --top;
   }
 }
@@ -567,10 +609,11 @@ __device__ __noinline__ void schur_solve(const Pol& Pl, const SchurWork& W, int 
 // (gohberg-semencul) from rho (as block_gs_apply); then rho = z1 / z1_{N-1},
 // dl = 1 / z1_{N-1}.  a (FP64) is read and rewritten in place (rho_n =
 // conj(a_{N-1-n})); c is the FP64 first column, inv_c0 = 1 / c_0.  Returns
-// the refined pivot of Ct.
+// the refined pivot of Ct.  A team (csize > 1) shares every step; c and a
+// are then in global memory.
 template <int NT, class Pol>
 __device__ double schur_refine(const Pol& Pl, const SchurWork& W, const c128* c, double inv_c0, c128* a, int N,
-                               double dl) {
+                               double dl, int crank = 0, int csize = 1) {
   using T = typename Pol::T;
   const int M2 = schur_refine_m(N);
   const int lg = ilog2((uint32_t)M2);
@@ -585,6 +628,7 @@ __device__ double schur_refine(const Pol& Pl, const SchurWork& W, const c128* c,
   const T inv_dl = Pol::of(mk(1.0 / dl, 0.0));
   const float inv = 1.0f / (float)M2;  // a power of two: exact
   const Pol P2 = Pl;
+  const int gt = crank * NT + (int)threadIdx.x, St = csize * NT;  // this thread in the team, the team's threads
   // transforms of rho and of the circulant's first column
   // [c_0..c_{N-1}, 0.., conj(c_{N-1})..conj(c_1)] (scaled by 1/c_0)
   pol_fft<NT, Pol>(
@@ -595,11 +639,12 @@ __device__ double schur_refine(const Pol& Pl, const SchurWork& W, const c128* c,
         if (i > M2 - N) return Pol::of(inv_c0 * conj(c[M2 - i]));
         return Pol::zero();
       },
-      P, tmp, lg, false);
+      P, tmp, lg, false, crank, csize);
   // Ct z0 (z0 = rho / dl), then r = e_{N-1} - Ct z0 and its transform
   pol_fft<NT, Pol>(
-      Pl, 1, [=] __device__(int, int w) { return (Pol::ld(H + w) * Pol::ld(P + w)) * inv_dl; }, R, UZ, lg, true);
-  for (int i = threadIdx.x; i < M2; i += NT) {
+      Pl, 1, [=] __device__(int, int w) { return (Pol::ld(H + w) * Pol::ld(P + w)) * inv_dl; }, R, UZ, lg, true, crank,
+      csize);
+  for (int i = gt; i < M2; i += St) {
     T v = Pol::zero();
     if (i < N) {
       v = Pol::scale2(-inv, Pol::ld(R + i));
@@ -607,8 +652,8 @@ __device__ double schur_refine(const Pol& Pl, const SchurWork& W, const c128* c,
     }
     Pol::st(R + i, v);
   }
-  __syncthreads();
-  pol_fft<NT, Pol>(Pl, 1, [=] __device__(int, int i) { return Pol::ld(R + i); }, H, UZ, lg, false);
+  team_sync(csize);
+  pol_fft<NT, Pol>(Pl, 1, [=] __device__(int, int i) { return Pol::ld(R + i); }, H, UZ, lg, false, crank, csize);
   // Ct^{-1} r by eq. (gohberg-semencul) as in block_gs_apply: u = T1 r and
   // z = T0^H r, truncated to N and transformed again, then T1^H u - T0 z
   pol_fft<NT, Pol>(
@@ -618,11 +663,11 @@ __device__ double schur_refine(const Pol& Pl, const SchurWork& W, const c128* c,
         if (j == 0) return rf * conj(P2.w((int)(((int64_t)(N - 1) * w) & msk), lg)) * p;
         return rf * conj(P2.w(w, lg)) * conj(p);
       },
-      UZ, tmp, lg, true);
+      UZ, tmp, lg, true, crank, csize);
   pol_fft<NT, Pol>(
       Pl, 2,
       [=] __device__(int j, int i) { return i < N ? Pol::scale2(inv, Pol::ld(UZ + (size_t)j * M2 + i)) : Pol::zero(); },
-      H, tmp, lg, false);
+      H, tmp, lg, false, crank, csize);
   pol_fft<NT, Pol>(
       Pl, 1,
       [=] __device__(int, int w) {
@@ -630,16 +675,16 @@ __device__ double schur_refine(const Pol& Pl, const SchurWork& W, const c128* c,
         const T g1 = P2.w((int)(((int64_t)(N - 1) * w) & msk), lg) * conj(p), g0 = P2.w(w, lg) * p;
         return g1 * Pol::ld(H + w) - g0 * Pol::ld(R + w);
       },
-      X, UZ, lg, true);
+      X, UZ, lg, true, crank, csize);
   // z1 = z0 + X / (M2 dl) = (rho + X / M2) / dl; rho' = z1 / z1_{N-1}, dl' = 1 / Re z1_{N-1}
   const c128 den = mk(1.0, 0.0) + Pol::to_c128(Pol::scale2(inv, Pol::ld(X + N - 1)));
   const double dd = norm2(den);
   const c128 inv_den = mk(den.re / dd, -den.im / dd);
-  for (int n = threadIdx.x; n < N; n += NT) {
+  for (int n = gt; n < N; n += St) {
     const c128 z = conj(a[N - 1 - n]) + Pol::to_c128(Pol::scale2(inv, Pol::ld(X + n)));
     a[N - 1 - n] = conj(z * inv_den);
   }
-  __syncthreads();
+  team_sync(csize);
   return dl / den.re;
 }
 
@@ -651,9 +696,15 @@ __device__ double schur_refine(const Pol& Pl, const SchurWork& W, const c128* c,
 // schur_workspace_elems(N) float4s (global), smem schur_smem_bytes(lsm) of
 // shared memory (lsm from schur_pick_lsm); sh_bad one shared int; sh_red NT/32 doubles and NT/32 ints
 // of shared memory.
+// A team of csize blocks of a cluster (this one of rank crank) shares the
+// recursion's global-memory FFT stages and the refinement: every block of the
+// team calls this with the same c, a, N, ws and lsm (c and a in global
+// memory, sh_bad and sh_rex at the same shared-memory offsets in every
+// block); rank 0's result is the one returned, the other ranks' is empty.
 template <int NT, class Pol>
 __device__ __noinline__ LevResult block_superfast(const Pol& Pl, const c128* c, c128* a, int N, float4* ws, float4* smem,
-                                     int lsm, int* sh_bad, double* sh_red, int* sh_rex) {
+                                     int lsm, int* sh_bad, double* sh_red, int* sh_rex, int crank = 0,
+                                     int csize = 1) {
   using T = typename Pol::T;
   static_assert(NT >= 96, "the leaves use three warps");
   SchurWork W = schur_carve(ws, N);
@@ -663,26 +714,45 @@ __device__ __noinline__ LevResult block_superfast(const Pol& Pl, const c128* c, 
   const bool c0_ok = c0 > 0.0 && isfinite(c0);
   const double inv_c0 = c0_ok ? 1.0 / c0 : 0.0;
   if (threadIdx.x == 0) *sh_bad = !c0_ok;
-  for (int t = threadIdx.x; t < N - 1; t += NT) {
+  for (int t = crank * NT + (int)threadIdx.x; t < N - 1; t += csize * NT) {
     Pol::st(W.Uw + t, Pol::of(inv_c0 * c[t + 1]));
     Pol::st(W.Vw + t, Pol::of(inv_c0 * c[t]));
   }
-  __syncthreads();
-  if (N > 1) schur_solve<NT, Pol>(Pl, W, N - 1);
-  // a = P + Q (the predictor of order N-1)
-  for (int i = threadIdx.x; i < N; i += NT)
-    a[i] = N > 1 ? Pol::to_c128(Pol::ld(W.Pc + i) + Pol::ld(W.Qc + i)) : mk(1.0, 0.0);
-  // ln|C| / c_0^N = sum_n ln(delta_n / c_0): a product kept as mantissa and
-  // exponent, in a fixed order; delta_{N-1} = delta_{N-2} (1 - |k_{N-1}|^2)
+  team_sync(csize);
+  if (N > 1) schur_solve<NT, Pol>(Pl, W, N - 1, crank, csize);
   double dlast = 1.0;
-  if (N > 1) {
-    const double dp = Pol::re_d(Pol::ld(W.delta + N - 2));
-    const c128 kl = Pol::to_c128(Pol::ld(W.ks + N - 2));
-    dlast = dp * (1.0 - norm2(kl));
+  bool refine = false;
+  if (crank == 0) {
+    // a = P + Q (the predictor of order N-1)
+    for (int i = threadIdx.x; i < N; i += NT)
+      a[i] = N > 1 ? Pol::to_c128(Pol::ld(W.Pc + i) + Pol::ld(W.Qc + i)) : mk(1.0, 0.0);
+    // ln|C| / c_0^N = sum_n ln(delta_n / c_0): a product kept as mantissa and
+    // exponent, in a fixed order; delta_{N-1} = delta_{N-2} (1 - |k_{N-1}|^2)
+    if (N > 1) {
+      const double dp = Pol::re_d(Pol::ld(W.delta + N - 2));
+      const c128 kl = Pol::to_c128(Pol::ld(W.ks + N - 2));
+      dlast = dp * (1.0 - norm2(kl));
+    }
+    __syncthreads();  // a complete, the leaves' flag visible
+    refine = N > 1 && !*sh_bad && dlast > 0.0 && isfinite(dlast);
   }
-  __syncthreads();  // a complete, the leaves' flag visible
-  if (N > 1 && !*sh_bad && dlast > 0.0 && isfinite(dlast))
-    dlast = schur_refine<NT, Pol>(Pl, W, c, inv_c0, a, N, dlast);
+  if (csize > 1) {
+    // rank 0 hands the decision and the pivot to the others (their sh_bad and
+    // sh_rex[0..1]; rank 0's own stay as they are)
+    if (crank == 0 && threadIdx.x == 0)
+      for (int r = 1; r < csize; ++r) {
+        st_cluster_u32(sh_bad, (unsigned)r, refine ? 1u : 0u);
+        st_cluster_u32(sh_rex, (unsigned)r, (unsigned)__double2loint(dlast));
+        st_cluster_u32(sh_rex + 1, (unsigned)r, (unsigned)__double2hiint(dlast));
+      }
+    cluster_barrier();  // a and the decision visible to the team
+    if (crank != 0) {
+      refine = *sh_bad != 0;
+      dlast = __hiloint2double(sh_rex[1], sh_rex[0]);
+    }
+  }
+  if (refine) dlast = schur_refine<NT, Pol>(Pl, W, c, inv_c0, a, N, dlast, crank, csize);
+  if (crank != 0) return LevResult{};
   double pm = 1.0;
   int pe = 0;
   for (int n = 1 + threadIdx.x; n < N; n += NT) {
