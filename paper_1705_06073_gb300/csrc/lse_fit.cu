@@ -303,18 +303,36 @@ struct Fitter {
       lr = block_levinson<kNT>(lev_c, lev_a, N, sh->red, &sh->lev);
     }
     if (threadIdx.x == 0) sh->n_evals++;
+    if (!lr.status)
+      for (int n = threadIdx.x; n < N; n += kNT) w.rho[n] = conj(lev_a[N - 1 - n]);
+    // a recursion shared with the other block of the cluster: the
+    // Gohberg-Semencul applies are shared too (the other block learns
+    // whether they run, and delta_{N-1}, in its sf_rex[2..4], words that
+    // the recursion's own hand-over does not use)
+    const bool paired = PREC == 2 && A->cluster == 2 && superfast();
+    if (paired) {
+      if (threadIdx.x == 0) {
+        st_cluster_u32(&sh->sf_rex[2], 1u, lr.status ? 0u : 1u);
+        st_cluster_u32(&sh->sf_rex[3], 1u, (unsigned)__double2loint(lr.delta_last));
+        st_cluster_u32(&sh->sf_rex[4], 1u, (unsigned)__double2hiint(lr.delta_last));
+      }
+      cluster_barrier();
+    }
     if (lr.status) {
       __syncthreads();
       return 1;
     }
-    for (int n = threadIdx.x; n < N; n += kNT) w.rho[n] = conj(lev_a[N - 1 - n]);
     __syncthreads();
     c128* bufs[5] = {w.buf[0], w.buf[1], w.buf[2], w.buf[3], w.buf[4]};
     double part = 0.0;
     for (int g = 0; g < G; ++g) {  // x_g = C^{-1} y_g, one Gohberg-Semencul apply per snapshot
       bool gs_done = false;
       if constexpr (PREC == 2) {  // double-float transforms when the table exists
-        if (A->tab.twdf) {
+        if (paired) {
+          team_gs_apply<kNT>(PolDF{A->tab.twdf, A->tab.log2max}, w.rho, w.Yfg(g), w.xg(g), N, log2M2, lr.delta_last,
+                             bufs, 0, 2);
+          gs_done = true;
+        } else if (A->tab.twdf) {
           block_gs_apply_df<kNT>(w.rho, w.Yfg(g), w.xg(g), N, log2M2, lr.delta_last, bufs,
                                  TwiddlesDF{A->tab.twdf, A->tab.log2max});
           gs_done = true;
@@ -1145,10 +1163,21 @@ __device__ void cluster_helper(FitShared<kNT>& sh, char* dsm, int csize, const F
       float4* smem;
       int lsm;
       superfast_smem(dsm, n, smem, lsm);
-      float4* sf = carve<typename Fitter<2>::TG>(args.ws + (size_t)unit * args.ws_bytes, args.Nmax, args.Lmax,
-                                                 args.cfg.G).sf;
-      block_superfast<kNT>(PolDF{args.tab.twdf, args.tab.log2max}, sh.cmd.c, sh.cmd.a, n, sf, smem, lsm, &sh.sf_bad,
-                           sh.dred, sh.sf_rex, 1, 2);
+      const Work<typename Fitter<2>::TG> w =
+          carve<typename Fitter<2>::TG>(args.ws + (size_t)unit * args.ws_bytes, args.Nmax, args.Lmax, args.cfg.G);
+      block_superfast<kNT>(PolDF{args.tab.twdf, args.tab.log2max}, sh.cmd.c, sh.cmd.a, n, w.sf, smem, lsm,
+                           &sh.sf_bad, sh.dred, sh.sf_rex, 1, 2);
+      // then this block's share of the Gohberg-Semencul applies, if the
+      // factorisation succeeded (the first block's words in sf_rex[2..4])
+      cluster_barrier();
+      if (sh.sf_rex[2]) {
+        const double delta_last = __hiloint2double(sh.sf_rex[4], sh.sf_rex[3]);
+        c128* bufs[5] = {w.buf[0], w.buf[1], w.buf[2], w.buf[3], w.buf[4]};
+        const int log2M2 = ilog2(2u * (uint32_t)n);
+        for (int g = 0; g < args.cfg.G; ++g)
+          team_gs_apply<kNT>(PolDF{args.tab.twdf, args.tab.log2max}, w.rho, w.Yfg(g), w.xg(g), n, log2M2, delta_last,
+                             bufs, 1, 2);
+      }
     } else {
       break;
     }

@@ -688,6 +688,62 @@ __device__ double schur_refine(const Pol& Pl, const SchurWork& W, const c128* c,
   return dl / den.re;
 }
 
+// ------------------------------------------------------------- GS apply --
+// x = C^{-1} y by eq. (gohberg-semencul) as FFT convolutions of length M2 =
+// 2^log2M2 >= 2N: the six transforms of block_gs_apply_df, each by pol_fft
+// (the same butterflies in the same order), so that a team of csize blocks
+// can share them.  rho, Yf = FFT_M2(y) and x in FP64 (global memory for a
+// team); bufs: 5 arrays of M2 16-byte elements (global memory).
+template <int NT, class Pol>
+__device__ void team_gs_apply(const Pol& Pl, const c128* rho, const c128* Yf, c128* x, int N, int log2M2,
+                              double delta_last, c128* const* bufs, int crank = 0, int csize = 1) {
+  using T = typename Pol::T;
+  const int M2 = 1 << log2M2;
+  const int msk = M2 - 1;
+  const float inv = 1.0f / (float)M2;  // a power of two: exact
+  const Pol P2 = Pl;
+  float4* P = reinterpret_cast<float4*>(bufs[0]);
+  float4* B1 = reinterpret_cast<float4*>(bufs[1]);
+  float4* B2 = reinterpret_cast<float4*>(bufs[2]);
+  float4* B3 = reinterpret_cast<float4*>(bufs[3]);
+  float4* Tm = reinterpret_cast<float4*>(bufs[4]);
+  pol_fft<NT, Pol>(
+      Pl, 1, [=] __device__(int, int i) { return i < N ? Pol::of(rho[i]) : Pol::zero(); }, P, Tm, log2M2, false,
+      crank, csize);
+  // u = T1 y
+  pol_fft<NT, Pol>(
+      Pl, 1,
+      [=] __device__(int, int w) {
+        return Pol::of(Yf[w]) * conj(P2.w((int)(((int64_t)(N - 1) * w) & msk), log2M2)) * Pol::ld(P + w);
+      },
+      B1, Tm, log2M2, true, crank, csize);
+  pol_fft<NT, Pol>(
+      Pl, 1, [=] __device__(int, int i) { return i < N ? Pol::scale2(inv, Pol::ld(B1 + i)) : Pol::zero(); }, B2, Tm,
+      log2M2, false, crank, csize);
+  // z = T0^H y
+  pol_fft<NT, Pol>(
+      Pl, 1, [=] __device__(int, int w) { return Pol::of(Yf[w]) * conj(P2.w(w, log2M2)) * conj(Pol::ld(P + w)); },
+      B1, Tm, log2M2, true, crank, csize);
+  pol_fft<NT, Pol>(
+      Pl, 1, [=] __device__(int, int i) { return i < N ? Pol::scale2(inv, Pol::ld(B1 + i)) : Pol::zero(); }, B3, Tm,
+      log2M2, false, crank, csize);
+  // x = (T1^H u - T0 z) / delta
+  pol_fft<NT, Pol>(
+      Pl, 1,
+      [=] __device__(int, int w) {
+        const T g1 = P2.w((int)(((int64_t)(N - 1) * w) & msk), log2M2) * conj(Pol::ld(P + w));
+        const T g0 = P2.w(w, log2M2) * Pol::ld(P + w);
+        return g1 * Pol::ld(B2 + w) - g0 * Pol::ld(B3 + w);
+      },
+      B1, Tm, log2M2, true, crank, csize);
+  const double sc = (double)inv / delta_last;
+  for (int i = crank * NT + (int)threadIdx.x; i < N; i += csize * NT) {
+    const c128 v = Pol::to_c128(Pol::ld(B1 + i));
+    x[i] = mk(sc * v.re, sc * v.im);
+  }
+  team_sync(csize);
+}
+
 // ------------------------------------------------------------- the block --
 // rho's predictor a (FP64, a_0 = 1) of the Hermitian positive definite
 // Toeplitz matrix with first column c (FP64), with delta_{N-1} and ln|C| =
