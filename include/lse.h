@@ -93,15 +93,19 @@ typedef struct lse_config {
 #define LSE_FLAG_NO_AUTOTUNE 1u
 
 /* Run every fit in one block per instance.  By default, on the double-float
- * path (LSE_PREC_MIXED_DF), a fit launch runs as thread-block clusters that
- * share each instance's Levinson recursion: of two blocks when every N is
- * small enough for the recursion to run in shared memory (N <= about 6000)
- * and the launch leaves a spare SM per instance (the second block takes half
- * of every order); of eight blocks, sharing the recursion's vectors in global
- * memory, when some N is larger and the launch leaves eight SMs per instance
- * (instances of that launch small enough for shared memory still run in one
- * block).  The results agree with the one-block launch to rounding (the
- * inner products are summed in a different order). */
+ * path (LSE_PREC_MIXED_DF), a fit launch whose batch leaves a spare SM per
+ * instance runs as two-block thread-block clusters.  For an instance on the
+ * superfast recursion (N >= 64) the second block takes half of every pass of
+ * the recursion's FFT stages kept in global memory, of its refinement step
+ * and of the Gohberg-Semencul applies; the results equal the one-block
+ * launch's bit for bit.  For an instance on the Levinson recursion the second
+ * block takes half of every order when the recursion fits in shared memory
+ * (N <= about 6000); when a batch with Levinson instances has a larger N and
+ * the launch leaves eight SMs per instance, the clusters have eight blocks
+ * sharing the recursion's vectors in global memory (instances small enough
+ * for shared memory, and superfast ones, then run in one block).  The
+ * Levinson results agree with the one-block launch to rounding (the inner
+ * products are summed in a different order). */
 #define LSE_FLAG_NO_CLUSTER 2u
 
 /* Run the O(N^2) Levinson-Durbin recursion for every N.  By default the

@@ -61,12 +61,17 @@ constexpr int kFactorCluster = 8;
 // cluster; the first block does everything and the others join its Levinson
 // recursion (csize 2: shared-memory copies; kFactorCluster: global memory,
 // for an instance too large for shared memory), or are released.
+// sf_pair (csize 2, every instance of the launch on the superfast recursion):
+// the second block follows the same steps, skipping the first block's own
+// work, and takes half of every pass of the recursion's global-memory FFT
+// stages and refinement, of the Gohberg-Semencul apply and of the two
+// omega_s transforms; the results are the one-block ones, bit for bit.
 template <bool DF>
 __global__ void __launch_bounds__(factor_threads<DF>(), 1)
     factor_kernel(const float* y, const InstDesc* inst, int Nmax, const double* theta, const double* gamma,
                   const double* beta, Tables tab, char* ws, size_t ws_bytes, c128* rho_out, c128* x_out,
                   c128* omega_out, c64* omega32_out, c64* x32_out, double* delta_out, int* status, int csize,
-                  int sf_min_n) {
+                  int sf_min_n, int sf_pair) {
   constexpr int kFNT = factor_threads<DF>();
   __shared__ c128 red[kFNT];
   __shared__ LevShared lev;
@@ -76,10 +81,13 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
   __shared__ int sf_rex[kFNT / 32];
   extern __shared__ __align__(16) char dsm[];
   int b = blockIdx.x;
+  int crank = 0;  // rank in a superfast pair
   if constexpr (DF) {
     if (csize > 1) {
       cluster_barrier();  // every block running before any store between them
-      if (cluster_ctarank() != 0) {
+      if (sf_pair) {
+        crank = (int)cluster_ctarank();
+      } else if (cluster_ctarank() != 0) {
         cluster_barrier();  // the request (or the release) is in cmd
         if (cmd.op == 1 && csize == 2) {
           // shared-memory recursion: copy the first block's double-float column
@@ -100,6 +108,7 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
   }
   const InstDesc d = inst[b];
   const int N = d.N;
+  const bool lead = crank == 0;
   char* base = ws + (size_t)b * ws_bytes;
   const FactorLayout FL = factor_layout(Nmax, sf_min_n > 0 && Nmax >= sf_min_n);
   // the superfast Schur recursion (lse_schur.cuh) for this instance?
@@ -113,7 +122,8 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
   const Twiddles<double> tw{tab.tw64, tab.log2max};
   const int log2M2 = ilog2(2u * (uint32_t)N);
   const float* yin = y + 2 * d.y_off;
-  for (int n = threadIdx.x; n < N; n += kFNT) yv[n] = mk((double)yin[2 * n], (double)yin[2 * n + 1]);
+  if (lead)
+    for (int n = threadIdx.x; n < N; n += kFNT) yv[n] = mk((double)yin[2 * n], (double)yin[2 * n + 1]);
   __syncthreads();
   int S, H;
   first_column_split(N, S, H);
@@ -125,12 +135,14 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
   } else {
     cc = (c128*)(base + FL.c); aa = (c128*)(base + FL.a); tables = (c128*)dsm;
   }
-  if constexpr (DF) block_first_column_df<kFNT>(cc, theta + d.k_off, gamma + d.k_off, d.K, beta[b], N, tables);
-  else block_first_column<kFNT>(cc, theta + d.k_off, gamma + d.k_off, d.K, beta[b], N, tables);
+  if (lead) {
+    if constexpr (DF) block_first_column_df<kFNT>(cc, theta + d.k_off, gamma + d.k_off, d.K, beta[b], N, tables);
+    else block_first_column<kFNT>(cc, theta + d.k_off, gamma + d.k_off, d.K, beta[b], N, tables);
+  }
   LevResult lr;
   if (sf) {
     // a cluster launch still owes its other blocks their release
-    if (DF && csize > 1) {
+    if (DF && csize > 1 && !sf_pair) {
       if (threadIdx.x == 0) lev_send_cmd(&cmd, csize, LevCmd{0, N, 0.0, cc, aa});
       cluster_barrier();
     }
@@ -138,9 +150,11 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
     const size_t tb = (tab_bytes + 255) & ~size_t(255);
     float4* sfs = reinterpret_cast<float4*>(dsm + tb);
     const int lsm = schur_pick_lsm(smem_cap - tb);
-    if constexpr (DF)
-      lr = block_superfast<kFNT>(PolDF{tab.twdf, tab.log2max}, cc, aa, N, sfw, sfs, lsm, &sf_bad, sf_red, sf_rex);
-    else
+    if constexpr (DF) {
+      if (sf_pair) cluster_barrier();  // the first column (global memory) complete
+      lr = block_superfast<kFNT>(PolDF{tab.twdf, tab.log2max}, cc, aa, N, sfw, sfs, lsm, &sf_bad, sf_red, sf_rex,
+                                 crank, sf_pair ? 2 : 1);
+    } else
       lr = block_superfast<kFNT>(Pol64{tab.tw64, tab.log2max}, cc, aa, N, sfw, sfs, lsm, &sf_bad, sf_red, sf_rex);
   } else if constexpr (DF) {
     if (csize > 1) {
@@ -176,19 +190,39 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
   }
   c128* rho = rho_out + d.y_off;
   c128* x = x_out + d.y_off;
+  if (lead && !lr.status) {
+    for (int n = threadIdx.x; n < N; n += kFNT) rho[n] = conj(aa[N - 1 - n]);
+    block_fft<kFNT, double>([=] __device__(int i) { return i < N ? yv[i] : zero<double>(); }, Yf, bufs[4], log2M2,
+                            false, tw);
+  }
+  const int tr = sf_pair ? crank : 0, ts = sf_pair ? 2 : 1;  // the pair shares the transforms below
+  if (sf_pair) {
+    // the second block learns whether they run, and delta_{N-1} (in its
+    // sf_rex[2..4], words the recursion's own hand-over does not use)
+    if (lead && threadIdx.x == 0) {
+      st_cluster_u32(&sf_rex[2], 1u, lr.status ? 0u : 1u);
+      st_cluster_u32(&sf_rex[3], 1u, (unsigned)__double2loint(lr.delta_last));
+      st_cluster_u32(&sf_rex[4], 1u, (unsigned)__double2hiint(lr.delta_last));
+    }
+    cluster_barrier();  // rho and Y = FFT(y) complete
+    if (!lead) {
+      lr.status = sf_rex[2] ? 0 : 1;
+      lr.delta_last = __hiloint2double(sf_rex[4], sf_rex[3]);
+    }
+  }
   if (lr.status) {
-    if (threadIdx.x == 0) { status[b] = 4; delta_out[b] = 0.0; }
-    for (int n = threadIdx.x; n < N; n += kFNT) { rho[n] = zero<double>(); x[n] = zero<double>(); }
+    if (lead) {
+      if (threadIdx.x == 0) { status[b] = 4; delta_out[b] = 0.0; }
+      for (int n = threadIdx.x; n < N; n += kFNT) { rho[n] = zero<double>(); x[n] = zero<double>(); }
+    }
     return;
   }
-  for (int n = threadIdx.x; n < N; n += kFNT) rho[n] = conj(aa[N - 1 - n]);
-  block_fft<kFNT, double>([=] __device__(int i) { return i < N ? yv[i] : zero<double>(); }, Yf, bufs[4], log2M2, false,
-                          tw);
   // double-float transforms (Gohberg-Semencul apply and the omega_s
   // correlation) when the table exists, else FP64
   bool dft = false;
   if constexpr (DF) dft = tab.twdf != nullptr;
-  if (dft) block_gs_apply_df<kFNT>(rho, Yf, x, N, log2M2, lr.delta_last, bufs, TwiddlesDF{tab.twdf, tab.log2max});
+  if (dft && sf_pair) team_gs_apply<kFNT>(PolDF{tab.twdf, tab.log2max}, rho, Yf, x, N, log2M2, lr.delta_last, bufs, tr, ts);
+  else if (dft) block_gs_apply_df<kFNT>(rho, Yf, x, N, log2M2, lr.delta_last, bufs, TwiddlesDF{tab.twdf, tab.log2max});
   else block_gs_apply<kFNT>(rho, Yf, x, N, log2M2, lr.delta_last, bufs, tw);
   // Diagonal sums of C^{-1} (Sec. III-C, Appendix B):
   //   omega_s(i) = (1/d) sum_q [(q-c) + (q+i-c)] rho_q conj(rho_{q+i}),  |i| < N,
@@ -207,22 +241,26 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
       float4* Pw = reinterpret_cast<float4*>(bufs[1]);
       float4* G = reinterpret_cast<float4*>(bufs[2]);
       float4* T = reinterpret_cast<float4*>(bufs[4]);
-      const TwiddlesDF twd{tab.twdf, tab.log2max};
+      const PolDF Pd{tab.twdf, tab.log2max};
       const f2 cen2 = f2{(float)cen, 0.f};  // a half-integer below 2^24: exact
-      block_fft_df<kFNT>(
-          [=] __device__(int i) {
+      // (pol_fft: the butterflies of block_fft_df, shared by a pair)
+      pol_fft<kFNT, PolDF>(
+          Pd, 1,
+          [=] __device__(int, int i) {
             if (i >= N) return cf2_zero();
             const cf2 r = cf2_of(rho[i]);
             const f2 wi = sub_s(f2{(float)i, 0.f}, cen2);
             return cf2{mul_f(wi, r.re), mul_f(wi, r.im)};
           },
-          Pw, T, log2M2, false, twd);
-      block_fft_df<kFNT>(
-          [=] __device__(int k) {
+          Pw, T, log2M2, false, tr, ts);
+      pol_fft<kFNT, PolDF>(
+          Pd, 1,
+          [=] __device__(int, int k) {
             const cf2 v = ld_cf2(Pw[k]) * conj(ld_cf2(P[k]));
             return cf2{f2{2.f * v.re.h, 2.f * v.re.l}, f2{0.f, 0.f}};
           },
-          G, T, log2M2, true, twd);
+          G, T, log2M2, true, tr, ts);
+      if (!lead) return;
       for (int i = (int)threadIdx.x - (N - 1); i <= N - 1; i += kFNT) {
         const cf2 g = ld_cf2(G[(-i) & msk]);
         const c128 v = mk(sc * to_d(g.re), sc * to_d(g.im));
@@ -521,10 +559,16 @@ static cudaError_t launch_factor_t(int sf_min_n, int Nmin, const float* y, const
   // shared memory and the launch leaves a spare SM per instance; of
   // kFactorCluster blocks when some recursion is too large for shared memory
   // and the launch leaves the SMs for them
-  int csize = 1;
-  // clusters serve the Levinson recursion only
+  int csize = 1, sf_pair = 0;
   const bool any_levinson = sf_min_n <= 0 || Nmin < sf_min_n || !tab.twdf;
-  if (DF && allow_cluster && any_levinson) {
+  if (DF && allow_cluster && !any_levinson) {  // pairs sharing the superfast recursions
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && 2 * B <= sms) {
+      csize = 2;
+      sf_pair = 1;
+    }
+  } else if (DF && allow_cluster) {
     int S, H;
     first_column_split(Nmax, S, H);
     const size_t need = 2 * sizeof(c128) * (size_t)Nmax + sizeof(c128) * kFirstColumnChunk * (S + H);
@@ -553,11 +597,11 @@ static cudaError_t launch_factor_t(int sf_min_n, int Nmin, const float* y, const
     lc.attrs = at;
     lc.numAttrs = 1;
     return cudaLaunchKernelEx(&lc, factor_kernel<DF>, y, inst, Nmax, theta, gamma, beta, tab, (char*)ws, wsb, rho_out,
-                              x_out, omega_out, omega32_out, x32_out, delta_out, status, csize, sf_min_n);
+                              x_out, omega_out, omega32_out, x32_out, delta_out, status, csize, sf_min_n, sf_pair);
   }
   factor_kernel<DF><<<B, factor_threads<DF>(), smem, stream>>>(y, inst, Nmax, theta, gamma, beta, tab, (char*)ws, wsb,
                                                                rho_out, x_out, omega_out, omega32_out, x32_out,
-                                                               delta_out, status, 1, sf_min_n);
+                                                               delta_out, status, 1, sf_min_n, 0);
   return cudaGetLastError();
 }
 

@@ -202,3 +202,54 @@ def test_grid_batch_mixing_on_chip_and_four_step_sizes(ctxs, which):
         err = grid_errors(got, ref, N)
         assert max(err.values()) < (1e-8 if f64 else 1e-4), (i, err)
         g0 += L
+
+
+def test_grid_superfast_pair_matches_one_block():
+    """On the double-float path a launch whose instances all take the
+    superfast recursion runs on two-block clusters: the second block takes
+    half of every pass of the recursion's global-memory FFT stages, its
+    refinement, the Gohberg-Semencul apply and the omega_s transforms.  Each
+    butterfly is computed as by one block, so the grid outputs equal those of
+    the one-block launch bit for bit (ragged N and L, twice in a row), and
+    they meet the FP32-grid bound against the oracle."""
+    import torch
+    from paper_1705_06073_gb300 import build, lse
+    build.build()
+    specs = [(1200, 10, 4096), (4096, 32, 16384), (300, 4, 1024), (2049, 16, 8192)]
+    ys, ths, gas, bes = [], [], [], []
+    for i, (N, K, L) in enumerate(specs):
+        y, th, ga, be = state(N, K, 3100 + i)
+        ys.append(y); ths.append(th); gas.append(ga); bes.append(be)
+    yo = np.concatenate([[0], np.cumsum([len(y) for y in ys])])
+    ko = np.concatenate([[0], np.cumsum([len(t) for t in ths])])
+    Ls = np.array([s[2] for s in specs], np.int32)
+    dev = torch.device("cuda:0")
+    y_d = torch.from_numpy(np.concatenate(ys)).to(dev)
+    th_d = torch.from_numpy(np.concatenate(ths)).to(dev)
+    ga_d = torch.from_numpy(np.concatenate(gas)).to(dev)
+    be_d = torch.tensor(bes, dtype=torch.float64, device=dev)
+    G = int(Ls.sum())
+    f64 = False  # a double-float context writes FP32 spectra
+    ct, rt = torch.complex64, torch.float32
+    res = {}
+    for flags in (0, lse.LSE_FLAG_NO_CLUSTER):
+        ctx = lse.lse_create(lse.lse_config_default(precision=lse.LSE_PREC_MIXED_DF, flags=flags))
+        try:
+            runs = []
+            for _ in range(2):
+                outs = {f: torch.zeros(G, dtype=ct if f in ("q", "dq", "d2q") else rt, device=dev) for f in FIELDS}
+                lse.lse_eval_grid_batch_d(ctx, y_d, yo, th_d, ga_d, ko, be_d, Ls, outs, f64=f64)
+                torch.cuda.synchronize()
+                runs.append({f: outs[f].cpu().numpy() for f in FIELDS})
+            res[flags] = runs
+        finally:
+            lse.lse_destroy(ctx)
+    for run in res[0]:
+        for f in FIELDS:
+            assert np.array_equal(run[f], res[lse.LSE_FLAG_NO_CLUSTER][0][f]), f
+    # and the paired launch still meets the oracle at the smallest instance
+    ref = dn.DenseEval(ys[2], ths[2], gas[2], bes[2]).grid(int(Ls[2]), derivatives=True)
+    g0 = int(Ls[0] + Ls[1])
+    got = {f: res[0][0][f][g0:g0 + Ls[2]] for f in FIELDS}
+    err = grid_errors(got, ref, specs[2][0])
+    assert max(err.values()) < 1e-4, err
