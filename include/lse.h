@@ -92,13 +92,16 @@ typedef struct lse_config {
  * capturing grid evaluations into a CUDA graph. */
 #define LSE_FLAG_NO_AUTOTUNE 1u
 
-/* Run every fit in one block per instance.  By default, on the double-float
- * path (LSE_PREC_MIXED_DF), a fit launch whose batch leaves a spare SM per
- * instance runs as two-block thread-block clusters.  For an instance on the
- * superfast recursion (N >= 64) the second block takes half of every pass of
- * the recursion's FFT stages kept in global memory, of its refinement step
- * and of the Gohberg-Semencul applies; the results equal the one-block
- * launch's bit for bit.  For an instance on the Levinson recursion the second
+/* Run every fit and eval-grid factorisation in one block per instance.  By
+ * default a launch whose batch leaves a spare SM per instance runs as
+ * two-block thread-block clusters: on every precision path when all its
+ * instances take the superfast recursion (N >= 64), and on the double-float
+ * path (LSE_PREC_MIXED_DF) also with Levinson instances.  For an instance on
+ * the superfast recursion the second block takes half of every pass of the
+ * recursion's FFT stages kept in global memory, of its refinement step and
+ * of the Gohberg-Semencul applies (and, in lse_eval_grid, of the omega_s
+ * transforms); the results equal the one-block launch's bit for bit.  For an
+ * instance on the Levinson recursion (double-float path) the second
  * block takes half of every order when the recursion fits in shared memory
  * (N <= about 6000); when a batch with Levinson instances has a larger N and
  * the launch leaves eight SMs per instance, the clusters have eight blocks

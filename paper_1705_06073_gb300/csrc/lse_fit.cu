@@ -282,19 +282,19 @@ struct Fitter {
     else block_first_column<kNT>(lev_c, th, ga, K, beta, N, tables);
     LevResult lr;
     if (superfast()) {
-      if constexpr (PREC == 2) {
-        if (A->cluster == 2) {  // shared with the other block of the cluster (c, a, w.sf in global memory)
-          if (threadIdx.x == 0) send_cmd(3, N, 0.0, lev_c, lev_a);
-          cluster_barrier();
-          lr = block_superfast<kNT>(PolDF{A->tab.twdf, A->tab.log2max}, lev_c, lev_a, N, w.sf, sf_smem, sf_lsm,
-                                    &sh->sf_bad, sh->dred, sh->sf_rex, 0, 2);
-        } else {
-          lr = block_superfast<kNT>(PolDF{A->tab.twdf, A->tab.log2max}, lev_c, lev_a, N, w.sf, sf_smem, sf_lsm,
-                                    &sh->sf_bad, sh->dred, sh->sf_rex);
-        }
-      } else
+      // on a two-block cluster the recursion is shared with the other block
+      // (c, a and w.sf are in global memory)
+      const int cs = A->cluster == 2 ? 2 : 1;
+      if (cs == 2) {
+        if (threadIdx.x == 0) send_cmd(3, N, 0.0, lev_c, lev_a);
+        cluster_barrier();
+      }
+      if constexpr (PREC == 2)
+        lr = block_superfast<kNT>(PolDF{A->tab.twdf, A->tab.log2max}, lev_c, lev_a, N, w.sf, sf_smem, sf_lsm,
+                                  &sh->sf_bad, sh->dred, sh->sf_rex, 0, cs);
+      else
         lr = block_superfast<kNT>(Pol64{A->tab.tw64, A->tab.log2max}, lev_c, lev_a, N, w.sf, sf_smem, sf_lsm,
-                                  &sh->sf_bad, sh->dred, sh->sf_rex);
+                                  &sh->sf_bad, sh->dred, sh->sf_rex, 0, cs);
     } else if constexpr (PREC == 2) {
       if (A->cluster == 2 && lev_smem) lr = cluster_levinson();
       else if (A->cluster == kBigCluster && !lev_smem) lr = cluster_levinson_big();
@@ -309,7 +309,7 @@ struct Fitter {
     // Gohberg-Semencul applies are shared too (the other block learns
     // whether they run, and delta_{N-1}, in its sf_rex[2..4], words that
     // the recursion's own hand-over does not use)
-    const bool paired = PREC == 2 && A->cluster == 2 && superfast();
+    const bool paired = A->cluster == 2 && superfast();
     if (paired) {
       if (threadIdx.x == 0) {
         st_cluster_u32(&sh->sf_rex[2], 1u, lr.status ? 0u : 1u);
@@ -338,7 +338,11 @@ struct Fitter {
           gs_done = true;
         }
       }
-      if (!gs_done) block_gs_apply<kNT>(w.rho, w.Yfg(g), w.xg(g), N, log2M2, lr.delta_last, bufs, tw64);
+      // FP64: the same transforms as block_gs_apply on the batched FFT, one
+      // block or shared by a pair
+      if (!gs_done)
+        team_gs_apply<kNT>(Pol64{A->tab.tw64, A->tab.log2max}, w.rho, w.Yfg(g), w.xg(g), N, log2M2, lr.delta_last,
+                           bufs, 0, paired ? 2 : 1);
       const c128 *yv = w.yg(g), *xv = w.xg(g);
       for (int n = threadIdx.x; n < N; n += kNT) part += (conj(yv[n]) * xv[n]).re;
     }
@@ -1143,30 +1147,42 @@ struct Fitter {
 // first block and run their share of each (double-float path only): a
 // Levinson recursion in shared memory (op 1) or global memory (op 2), or the
 // global-memory FFT stages and the refinement of a superfast one (op 3).
-template <int kNT>
+template <int PREC, int kNT = threads_for<PREC>()>
 __device__ void cluster_helper(FitShared<kNT>& sh, char* dsm, int csize, const FitArgs& args, int unit) {
   for (;;) {
     cluster_barrier();  // a request (or the end) is in sh.cmd
     const int op = sh.cmd.op, n = sh.cmd.N;
     const double c0 = sh.cmd.c0;
-    if (op == 1 && csize == 2) {
-      c128* c = reinterpret_cast<c128*>(dsm);
-      c128* a = c + n;
-      const unsigned src = cluster_addr(c, 0u);
-      float4* c4 = reinterpret_cast<float4*>(c);
-      for (int i = threadIdx.x; i < n; i += kNT) c4[i] = ld_cluster(src + 16u * (unsigned)i);
-      __syncthreads();
-      cluster_levinson_df<kNT>(c, a, n, c0, (float4*)sh.red, &sh.lev);
-    } else if (op == 2 && csize == kBigCluster) {
-      cluster_levinson_global<kNT, kBigCluster>(sh.cmd.c, sh.cmd.a, n, c0, (float4*)sh.red, &sh.lev);
+    bool lev = false;  // a Levinson request (double-float path only)
+    if constexpr (PREC == 2) {
+      if (op == 1 && csize == 2) {
+        c128* c = reinterpret_cast<c128*>(dsm);
+        c128* a = c + n;
+        const unsigned src = cluster_addr(c, 0u);
+        float4* c4 = reinterpret_cast<float4*>(c);
+        for (int i = threadIdx.x; i < n; i += kNT) c4[i] = ld_cluster(src + 16u * (unsigned)i);
+        __syncthreads();
+        cluster_levinson_df<kNT>(c, a, n, c0, (float4*)sh.red, &sh.lev);
+        lev = true;
+      } else if (op == 2 && csize == kBigCluster) {
+        cluster_levinson_global<kNT, kBigCluster>(sh.cmd.c, sh.cmd.a, n, c0, (float4*)sh.red, &sh.lev);
+        lev = true;
+      }
+    }
+    if (lev) {
+      continue;
     } else if (op == 3 && csize == 2) {
       float4* smem;
       int lsm;
       superfast_smem(dsm, n, smem, lsm);
-      const Work<typename Fitter<2>::TG> w =
-          carve<typename Fitter<2>::TG>(args.ws + (size_t)unit * args.ws_bytes, args.Nmax, args.Lmax, args.cfg.G);
-      block_superfast<kNT>(PolDF{args.tab.twdf, args.tab.log2max}, sh.cmd.c, sh.cmd.a, n, w.sf, smem, lsm,
-                           &sh.sf_bad, sh.dred, sh.sf_rex, 1, 2);
+      using TG = typename Fitter<PREC>::TG;
+      const Work<TG> w = carve<TG>(args.ws + (size_t)unit * args.ws_bytes, args.Nmax, args.Lmax, args.cfg.G);
+      if constexpr (PREC == 2)
+        block_superfast<kNT>(PolDF{args.tab.twdf, args.tab.log2max}, sh.cmd.c, sh.cmd.a, n, w.sf, smem, lsm,
+                             &sh.sf_bad, sh.dred, sh.sf_rex, 1, 2);
+      else
+        block_superfast<kNT>(Pol64{args.tab.tw64, args.tab.log2max}, sh.cmd.c, sh.cmd.a, n, w.sf, smem, lsm,
+                             &sh.sf_bad, sh.dred, sh.sf_rex, 1, 2);
       // then this block's share of the Gohberg-Semencul applies, if the
       // factorisation succeeded (the first block's words in sf_rex[2..4])
       cluster_barrier();
@@ -1174,9 +1190,14 @@ __device__ void cluster_helper(FitShared<kNT>& sh, char* dsm, int csize, const F
         const double delta_last = __hiloint2double(sh.sf_rex[4], sh.sf_rex[3]);
         c128* bufs[5] = {w.buf[0], w.buf[1], w.buf[2], w.buf[3], w.buf[4]};
         const int log2M2 = ilog2(2u * (uint32_t)n);
-        for (int g = 0; g < args.cfg.G; ++g)
-          team_gs_apply<kNT>(PolDF{args.tab.twdf, args.tab.log2max}, w.rho, w.Yfg(g), w.xg(g), n, log2M2, delta_last,
-                             bufs, 1, 2);
+        for (int g = 0; g < args.cfg.G; ++g) {
+          if constexpr (PREC == 2)
+            team_gs_apply<kNT>(PolDF{args.tab.twdf, args.tab.log2max}, w.rho, w.Yfg(g), w.xg(g), n, log2M2,
+                               delta_last, bufs, 1, 2);
+          else
+            team_gs_apply<kNT>(Pol64{args.tab.tw64, args.tab.log2max}, w.rho, w.Yfg(g), w.xg(g), n, log2M2,
+                               delta_last, bufs, 1, 2);
+        }
       }
     } else {
       break;
@@ -1190,15 +1211,13 @@ __global__ void __launch_bounds__(threads_for<PREC>(), 1) fit_kernel(FitArgs arg
   __shared__ FitShared<threads_for<PREC>()> sh;
   extern __shared__ __align__(16) char dsm[];
   int unit = blockIdx.x;  // workspace index
-  if constexpr (PREC == 2) {
-    if (args.cluster) {
-      cluster_barrier();  // both blocks running before any shared-memory store between them
-      if (cluster_ctarank() != 0) {
-        cluster_helper<threads_for<PREC>()>(sh, dsm, args.cluster, args, (int)(blockIdx.x / args.cluster));
-        return;
-      }
-      unit = blockIdx.x / args.cluster;
+  if (args.cluster) {
+    cluster_barrier();  // both blocks running before any shared-memory store between them
+    if (cluster_ctarank() != 0) {
+      cluster_helper<PREC>(sh, dsm, args.cluster, args, (int)(blockIdx.x / args.cluster));
+      return;
     }
+    unit = blockIdx.x / args.cluster;
   }
   Fitter<PREC> F;
   F.sh = &sh;
@@ -1216,11 +1235,9 @@ __global__ void __launch_bounds__(threads_for<PREC>(), 1) fit_kernel(FitArgs arg
     if (b >= args.B) break;
     F.run(b);
   }
-  if constexpr (PREC == 2) {
-    if (args.cluster) {  // release the other blocks
-      if (threadIdx.x == 0) F.send_cmd(0, 0, 0.0, nullptr, nullptr);
-      cluster_barrier();
-    }
+  if (args.cluster) {  // release the other blocks
+    if (threadIdx.x == 0) F.send_cmd(0, 0, 0.0, nullptr, nullptr);
+    cluster_barrier();
   }
 }
 
@@ -1306,10 +1323,12 @@ cudaError_t launch_fit(int prec, const float* y, const InstDesc* inst, int B, in
   // sharing the recursions of the instances too large for shared memory
   // through global memory, when the batch leaves kBigCluster SMs per instance.
   // Instances that run the superfast recursion share its global-memory FFT
-  // stages and refinement with the second block of a two-block cluster.
+  // stages, its refinement and the Gohberg-Semencul applies with the second
+  // block of a two-block cluster (every precision; on the FP64 and mixed
+  // paths when every instance of the launch runs the superfast recursion).
   a.cluster = 0;
-  const bool any_levinson = cfg.sf_min_n <= 0 || cfg.Nmin < cfg.sf_min_n || !tab.twdf;
-  if (prec == 2 && cfg.cluster) {
+  const bool any_levinson = cfg.sf_min_n <= 0 || cfg.Nmin < cfg.sf_min_n || (prec == 2 && !tab.twdf);
+  if (cfg.cluster && (prec == 2 || !any_levinson)) {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {

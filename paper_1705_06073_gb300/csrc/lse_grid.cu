@@ -57,10 +57,11 @@ __host__ __device__ inline FactorLayout factor_layout(int Nmax, bool sf) {
 // blocks per cluster for large-N recursions of the double-float factor kernel
 constexpr int kFactorCluster = 8;
 
-// csize > 1 (double-float only): clusters of csize blocks, one instance per
-// cluster; the first block does everything and the others join its Levinson
-// recursion (csize 2: shared-memory copies; kFactorCluster: global memory,
-// for an instance too large for shared memory), or are released.
+// csize > 1: clusters of csize blocks, one instance per cluster.  Levinson
+// clusters (double-float only): the first block does everything and the
+// others join its Levinson recursion (csize 2: shared-memory copies;
+// kFactorCluster: global memory, for an instance too large for shared
+// memory), or are released.
 // sf_pair (csize 2, every instance of the launch on the superfast recursion):
 // the second block follows the same steps, skipping the first block's own
 // work, and takes half of every pass of the recursion's global-memory FFT
@@ -82,12 +83,12 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
   extern __shared__ __align__(16) char dsm[];
   int b = blockIdx.x;
   int crank = 0;  // rank in a superfast pair
-  if constexpr (DF) {
-    if (csize > 1) {
-      cluster_barrier();  // every block running before any store between them
-      if (sf_pair) {
-        crank = (int)cluster_ctarank();
-      } else if (cluster_ctarank() != 0) {
+  if (csize > 1) {
+    cluster_barrier();  // every block running before any store between them
+    if (sf_pair) {
+      crank = (int)cluster_ctarank();
+    } else if (cluster_ctarank() != 0) {
+      if constexpr (DF) {  // Levinson clusters: double-float only
         cluster_barrier();  // the request (or the release) is in cmd
         if (cmd.op == 1 && csize == 2) {
           // shared-memory recursion: copy the first block's double-float column
@@ -101,10 +102,10 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
         } else if (cmd.op == 2 && csize == kFactorCluster) {
           cluster_levinson_global<kFNT, kFactorCluster>(cmd.c, cmd.a, cmd.N, cmd.c0, (float4*)red, &lev);
         }
-        return;
       }
-      b = blockIdx.x / csize;
+      return;
     }
+    b = blockIdx.x / csize;
   }
   const InstDesc d = inst[b];
   const int N = d.N;
@@ -150,12 +151,13 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
     const size_t tb = (tab_bytes + 255) & ~size_t(255);
     float4* sfs = reinterpret_cast<float4*>(dsm + tb);
     const int lsm = schur_pick_lsm(smem_cap - tb);
-    if constexpr (DF) {
-      if (sf_pair) cluster_barrier();  // the first column (global memory) complete
+    if (sf_pair) cluster_barrier();  // the first column (global memory) complete
+    if constexpr (DF)
       lr = block_superfast<kFNT>(PolDF{tab.twdf, tab.log2max}, cc, aa, N, sfw, sfs, lsm, &sf_bad, sf_red, sf_rex,
                                  crank, sf_pair ? 2 : 1);
-    } else
-      lr = block_superfast<kFNT>(Pol64{tab.tw64, tab.log2max}, cc, aa, N, sfw, sfs, lsm, &sf_bad, sf_red, sf_rex);
+    else
+      lr = block_superfast<kFNT>(Pol64{tab.tw64, tab.log2max}, cc, aa, N, sfw, sfs, lsm, &sf_bad, sf_red, sf_rex,
+                                 crank, sf_pair ? 2 : 1);
   } else if constexpr (DF) {
     if (csize > 1) {
       // exactly one request per launch: the shared recursion, or a release
@@ -223,7 +225,8 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
   if constexpr (DF) dft = tab.twdf != nullptr;
   if (dft && sf_pair) team_gs_apply<kFNT>(PolDF{tab.twdf, tab.log2max}, rho, Yf, x, N, log2M2, lr.delta_last, bufs, tr, ts);
   else if (dft) block_gs_apply_df<kFNT>(rho, Yf, x, N, log2M2, lr.delta_last, bufs, TwiddlesDF{tab.twdf, tab.log2max});
-  else block_gs_apply<kFNT>(rho, Yf, x, N, log2M2, lr.delta_last, bufs, tw);
+  else  // FP64: the same transforms as block_gs_apply on the batched FFT, one block or shared by a pair
+    team_gs_apply<kFNT>(Pol64{tab.tw64, tab.log2max}, rho, Yf, x, N, log2M2, lr.delta_last, bufs, tr, ts);
   // Diagonal sums of C^{-1} (Sec. III-C, Appendix B):
   //   omega_s(i) = (1/d) sum_q [(q-c) + (q+i-c)] rho_q conj(rho_{q+i}),  |i| < N,
   // two cross-correlations; with P = FFT(rho) (still in bufs[0] after the
@@ -271,10 +274,15 @@ __global__ void __launch_bounds__(factor_threads<DF>(), 1)
       const c128* P = bufs[0];
       c128* Pw = bufs[1];
       c128* G = bufs[2];
-      block_fft<kFNT, double>([=] __device__(int i) { return i < N ? ((double)i - cen) * rho[i] : zero<double>(); },
-                              Pw, bufs[4], log2M2, false, tw);
-      block_fft<kFNT, double>([=] __device__(int k) { return mk(2.0 * (Pw[k] * conj(P[k])).re, 0.0); }, G, bufs[4],
-                              log2M2, true, tw);
+      const Pol64 P6{tab.tw64, tab.log2max};
+      // (pol_fft: the butterflies of block_fft, shared by a pair)
+      pol_fft<kFNT, Pol64>(
+          P6, 1, [=] __device__(int, int i) { return i < N ? ((double)i - cen) * rho[i] : zero<double>(); },
+          reinterpret_cast<float4*>(Pw), reinterpret_cast<float4*>(bufs[4]), log2M2, false, tr, ts);
+      pol_fft<kFNT, Pol64>(
+          P6, 1, [=] __device__(int, int k) { return mk(2.0 * (Pw[k] * conj(P[k])).re, 0.0); },
+          reinterpret_cast<float4*>(G), reinterpret_cast<float4*>(bufs[4]), log2M2, true, tr, ts);
+      if (!lead) return;
       for (int i = (int)threadIdx.x - (N - 1); i <= N - 1; i += kFNT) {
         const c128 v = sc * G[(-i) & msk];
         om[i + N - 1] = v;
@@ -560,8 +568,8 @@ static cudaError_t launch_factor_t(int sf_min_n, int Nmin, const float* y, const
   // kFactorCluster blocks when some recursion is too large for shared memory
   // and the launch leaves the SMs for them
   int csize = 1, sf_pair = 0;
-  const bool any_levinson = sf_min_n <= 0 || Nmin < sf_min_n || !tab.twdf;
-  if (DF && allow_cluster && !any_levinson) {  // pairs sharing the superfast recursions
+  const bool any_levinson = sf_min_n <= 0 || Nmin < sf_min_n || (DF && !tab.twdf);
+  if (allow_cluster && !any_levinson) {  // pairs sharing the superfast recursions (every precision)
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && 2 * B <= sms) {
@@ -612,7 +620,7 @@ cudaError_t launch_factor(bool df, int sf_min_n, int Nmin, const float* y, const
   return df ? launch_factor_t<true>(sf_min_n, Nmin, y, inst, B, Nmax, theta, gamma, beta, tab, ws, rho_out, x_out,
                                     omega_out, omega32_out, x32_out, delta_out, status, allow_cluster, stream)
             : launch_factor_t<false>(sf_min_n, Nmin, y, inst, B, Nmax, theta, gamma, beta, tab, ws, rho_out, x_out,
-                                     omega_out, omega32_out, x32_out, delta_out, status, false, stream);
+                                     omega_out, omega32_out, x32_out, delta_out, status, allow_cluster, stream);
 }
 
 size_t grid_workspace_bytes(size_t ws_elems, bool f32) { return ws_elems * (f32 ? sizeof(c64) : sizeof(c128)); }

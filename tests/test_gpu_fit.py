@@ -222,20 +222,21 @@ def test_superfast_matches_levinson():
         assert abs(a["beta"] - b["beta"]) <= 1e-8 * b["beta"]
 
 
-def test_superfast_pair_matches_one_block():
-    """On the double-float path a small batch runs every superfast recursion
-    on a two-block cluster: the second block takes half of every pass of the
-    FFT stages kept in global memory and of the refinement.  Each butterfly is
-    computed as by one block, so the fits equal the one-block fits bit for bit
-    (instances whose recursion has one, two and three global-memory levels,
-    and a ragged N)."""
+@pytest.mark.parametrize("prec", ["mixed_df", "fp64", "mixed"])
+def test_superfast_pair_matches_one_block(prec):
+    """A small batch runs every superfast recursion on a two-block cluster:
+    the second block takes half of every pass of the FFT stages kept in
+    global memory, of the refinement and of the Gohberg-Semencul applies.
+    Each butterfly is computed as by one block, so the fits equal the
+    one-block fits bit for bit (instances whose recursion has one, two and
+    three global-memory levels, and a ragged N), on every precision path."""
     from paper_1705_06073_gb300 import build, lse
     build.build()
     specs = [(1200, 12, 25.0), (2049, 24, 15.0), (4096, 64, 20.0), (8192, 64, 30.0), (300, 6, 20.0)]
     insts = [synth.make_instance(N, K, snr, 8600 + i) for i, (N, K, snr) in enumerate(specs)]
     res = {}
     for flags in (0, lse.LSE_FLAG_NO_CLUSTER):
-        ctx = lse.lse_create(lse.lse_config_default(precision=lse.LSE_PREC_MIXED_DF, flags=flags))
+        ctx = lse.lse_create(lse.lse_config_default(precision=prec_of(lse, prec), flags=flags))
         try:
             res[flags] = lse.lse_fit_batch(ctx, [i.y for i in insts])
             res[flags] = (res[flags], lse.lse_fit_batch(ctx, [i.y for i in insts]))  # twice: no state left behind

@@ -204,14 +204,15 @@ def test_grid_batch_mixing_on_chip_and_four_step_sizes(ctxs, which):
         g0 += L
 
 
-def test_grid_superfast_pair_matches_one_block():
-    """On the double-float path a launch whose instances all take the
-    superfast recursion runs on two-block clusters: the second block takes
+@pytest.mark.parametrize("prec", ["mixed_df", "fp64", "mixed"])
+def test_grid_superfast_pair_matches_one_block(prec):
+    """A launch whose instances all take the superfast recursion runs on
+    two-block clusters (every precision path): the second block takes
     half of every pass of the recursion's global-memory FFT stages, its
     refinement, the Gohberg-Semencul apply and the omega_s transforms.  Each
     butterfly is computed as by one block, so the grid outputs equal those of
     the one-block launch bit for bit (ragged N and L, twice in a row), and
-    they meet the FP32-grid bound against the oracle."""
+    they meet the grid bound of the path against the oracle."""
     import torch
     from paper_1705_06073_gb300 import build, lse
     build.build()
@@ -229,11 +230,12 @@ def test_grid_superfast_pair_matches_one_block():
     ga_d = torch.from_numpy(np.concatenate(gas)).to(dev)
     be_d = torch.tensor(bes, dtype=torch.float64, device=dev)
     G = int(Ls.sum())
-    f64 = False  # a double-float context writes FP32 spectra
-    ct, rt = torch.complex64, torch.float32
+    f64 = prec == "fp64"  # an FP64 context writes FP64 spectra, the others FP32
+    ct, rt = (torch.complex128, torch.float64) if f64 else (torch.complex64, torch.float32)
+    precision = {"mixed_df": lse.LSE_PREC_MIXED_DF, "fp64": lse.LSE_PREC_FP64, "mixed": lse.LSE_PREC_MIXED}[prec]
     res = {}
     for flags in (0, lse.LSE_FLAG_NO_CLUSTER):
-        ctx = lse.lse_create(lse.lse_config_default(precision=lse.LSE_PREC_MIXED_DF, flags=flags))
+        ctx = lse.lse_create(lse.lse_config_default(precision=precision, flags=flags))
         try:
             runs = []
             for _ in range(2):
@@ -252,4 +254,4 @@ def test_grid_superfast_pair_matches_one_block():
     g0 = int(Ls[0] + Ls[1])
     got = {f: res[0][0][f][g0:g0 + Ls[2]] for f in FIELDS}
     err = grid_errors(got, ref, specs[2][0])
-    assert max(err.values()) < 1e-4, err
+    assert max(err.values()) < (1e-8 if f64 else 1e-4), err
