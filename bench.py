@@ -740,7 +740,12 @@ def main():
     from paper_1705_06073_gb300 import lse, synth
 
     Bn = args.batch
-    insts = synth.batch64_n4096(seed0=201 + 100000 * rank, B=Bn)
+    # weak scaling: a batch of Bn instances per rank, drawn as one batch of
+    # Bn x world instances and split by the host-side sharding (no collective
+    # on the data path); one rank fits exactly the single-GPU batch
+    from paper_1705_06073_gb300 import shard
+    everything = synth.batch64_n4096(seed0=201, B=Bn * world)
+    insts = [everything[i] for i in shard.rank_shard([inst.N for inst, _ in everything], world, rank)]
     ys = [i.y for i, _ in insts]
     offsets = np.concatenate([[0], np.cumsum([len(y) for y in ys])]).astype(np.int64)
     y_host = np.ascontiguousarray(np.concatenate(ys))

@@ -25,9 +25,12 @@ def test_balanced_shards_cover_every_instance_once():
         sh = shard.balanced_shards(sizes, world)
         flat = sorted(i for s in sh for i in s)
         assert flat == list(range(len(sizes)))
-        loads = [sum(sizes[i] ** 2 for i in s) for s in sh]
+        loads = [sum(shard.fit_cost(sizes[i]) for i in s) for s in sh]
         # LPT bound: no rank exceeds the ideal share by more than the largest job
-        assert max(loads) <= sum(loads) / world + max(s ** 2 for s in sizes)
+        assert max(loads) <= sum(loads) / world + max(shard.fit_cost(s) for s in sizes)
+    # equal instances split evenly, and one rank takes everything in order
+    assert [len(s) for s in shard.balanced_shards([4096] * 128, 4)] == [32] * 4
+    assert shard.balanced_shards([4096] * 64, 1) == [list(range(64))]
 
 
 def _worker(rank, world, port, q):
