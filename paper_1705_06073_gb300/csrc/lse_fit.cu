@@ -2,11 +2,14 @@
 // block-coordinate-descent estimator (Sec. II-D, II-E of Hansen, Fleury,
 // Rao, "Superfast Line Spectral Estimation") for one instance at a time,
 // pulling instances from a device work counter, with every model evaluation
-// done by the superfast route of Sec. III (Levinson recursion for the
-// Gohberg-Semencul generators, FFT convolutions, FFT grid, direct off-grid
-// sums).  On the double-float path a small batch runs as thread-block
-// clusters: the first block of each cluster runs the estimator and the other
-// blocks only take their share of every Levinson recursion.
+// done by the superfast route of Sec. III (superfast Schur or Levinson
+// recursion for the Gohberg-Semencul generators, FFT convolutions, FFT grid,
+// direct or non-uniform-FFT off-grid sums).  A batch that leaves a spare SM
+// per instance runs as thread-block clusters: the first block of each
+// cluster runs the estimator and the other blocks only take their share of
+// the work it hands over (the superfast recursion's global-memory FFT passes,
+// its refinement and the Gohberg-Semencul applies, on every precision path;
+// on the double-float path also the Levinson recursion).
 //
 // Readings of the paper (the same ones the CPU oracle follows):
 //  - (theta, gamma) update: one per-component diagonal Newton step with the

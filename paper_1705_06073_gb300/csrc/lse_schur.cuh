@@ -2,7 +2,9 @@
 // definite Toeplitz matrix by a divide-and-conquer ("superfast") Schur
 // recursion: O(N log^2 N) work instead of the O(N^2) Levinson-Durbin
 // recursion, which the paper names as the faster alternative for large N
-// (Sec. III intro; Sec. III-E), organised for one thread block.
+// (Sec. III intro; Sec. III-E), organised for one thread block, or for a
+// pair of blocks in a thread-block cluster sharing the passes of the FFT
+// stages kept in global memory (the "team" arguments below).
 //
 // Notation (the same as block_levinson).  C has first column c; the order-n
 // predictor a^(n) (a_0 = 1) and its reversed conjugate b^(n)_i =
